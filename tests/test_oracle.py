@@ -1,0 +1,287 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle itself.
+
+Every oracle function is checked here against at least one of: a hand-worked
+fixture (tests/golden), a closed form, an invariant of the definition, a
+published known-answer vector, exact big-integer arithmetic, or brute force
+over all pairs.  test_mutants_fail_pins recompiles the oracle with planted
+mistakes and checks that these pins catch each one.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import bits_synth as synth
+import oracle
+from goldens import read_count_fixture, read_philox_kat
+
+O = oracle.get()
+
+
+# ------------------------------------------------------------ counting (Sec. 1.1, Alg. 1, Alg. 2)
+
+@pytest.mark.parametrize("name", ["containment.txt", "duplicates.txt"])
+def test_golden_fixture(name):
+    a, b, exp, total = read_count_fixture(name)
+    c, t = O.count_brute(a, b)
+    np.testing.assert_array_equal(c, exp)
+    assert t == total
+    c2, t2 = O.count(a, b)
+    np.testing.assert_array_equal(c2, exp)
+    assert t2 == total
+
+
+def test_closed_form_unit_tiles():
+    m = 50
+    b = synth.unit_tiles(m)
+    rng = np.random.default_rng(0)
+    s = rng.integers(0, 70, size=400)
+    e = s + rng.integers(0, 20, size=400)
+    a = np.stack([s, e], 1).astype(np.uint32)
+    expect = np.maximum(0, np.minimum(e, m) - np.maximum(s, 0))
+    expect[s == e] = 0
+    for fn in (O.count_brute, O.count):
+        c, t = fn(a, b)
+        np.testing.assert_array_equal(c, expect)
+        assert t == int(expect.sum())
+
+
+def test_closed_form_nested():
+    # [i, 2m-i) for i < m; the point query [x, x+1) meets min(x+1, 2m-x) of them.
+    m = 40
+    b = synth.nested(m)
+    x = np.arange(0, 2 * m + 5)
+    a = np.stack([x, x + 1], 1).astype(np.uint32)
+    expect = np.clip(np.minimum(x + 1, 2 * m - x), 0, m)
+    for fn in (O.count_brute, O.count):
+        c, _ = fn(a, b)
+        np.testing.assert_array_equal(c, expect)
+
+
+def test_all_of_b_in_one_interval():
+    b = np.array([[0, 1000]] * 7 + [[10, 20]], np.uint32)
+    a = np.array([[500, 501], [15, 15], [0, 0], [1000, 1001], [999, 1000]], np.uint32)
+    c, _ = O.count(a, b)
+    np.testing.assert_array_equal(c, [7, 8, 0, 0, 7])
+
+
+def test_sorted_matches_brute_tiny_random():
+    for seed in range(400):
+        rng = np.random.default_rng(seed)
+        na, nb = int(rng.integers(0, 30)), int(rng.integers(0, 30))
+        a, b = synth.tiny_random(seed, na, nb, coord_max=int(rng.integers(2, 80)),
+                                 max_len=int(rng.integers(1, 12)))
+        c1, t1 = O.count_brute(a, b)
+        c2, t2 = O.count(a, b)
+        np.testing.assert_array_equal(c1, c2)
+        assert t1 == t2 == int(c1.sum())
+        assert (c1 <= nb).all()
+
+
+def test_invariants():
+    rng = np.random.default_rng(7)
+    for seed in range(60):
+        a, b = synth.tiny_random(1000 + seed, 25, 30, coord_max=200, max_len=30,
+                                 allow_empty_queries=False)
+        _, t_ab = O.count(a, b)
+        _, t_ba = O.count(b, a)
+        assert t_ab == t_ba                                   # symmetric predicate
+        shift = int(rng.integers(1, 1 << 30))
+        _, t_sh = O.count(a + np.uint32(shift), b + np.uint32(shift))
+        assert t_sh == t_ab                                   # translation invariance
+        far = b + np.uint32(10_000)
+        _, t_far = O.count(a, far)
+        assert t_far == 0                                     # disjoint contigs
+        k = int(rng.integers(1, b.shape[0]))
+        _, t1 = O.count(a, b[:k])
+        _, t2 = O.count(a, b[k:])
+        assert t1 + t2 == t_ab                                # additive over splits of B
+        k = int(rng.integers(1, a.shape[0]))
+        _, t3 = O.count(a[:k], b)
+        _, t4 = O.count(a[k:], b)
+        assert t3 + t4 == t_ab                                # additive over splits of A
+        c, _ = O.count(a, b)
+        assert ((c > 0).any()) == (t_ab > 0)                  # decision problem
+
+
+def test_config1_full_brute_force():
+    a, b = synth.config1()
+    c1, t1 = O.count_brute(a, b)
+    c2, t2 = O.count(a, b)
+    np.testing.assert_array_equal(c1, c2)
+    assert t1 == t2
+
+
+def test_threads_do_not_change_result():
+    _, a, b = synth.config2(n_a=20_000, n_b=200_000, n_hot=2000)
+    bs, be = O.build(b)
+    c1, t1 = O.count_sorted(a, bs, be, threads=1)
+    c4, t4 = O.count_sorted(a, bs, be, threads=4)
+    np.testing.assert_array_equal(c1, c4)
+    assert t1 == t4
+
+
+def test_build_is_sorted_permutation():
+    b = synth.config1()[1]
+    bs, be = O.build(b)
+    assert (np.diff(bs.astype(np.int64)) >= 0).all() and (np.diff(be.astype(np.int64)) >= 0).all()
+    np.testing.assert_array_equal(np.sort(b[:, 0]), bs)
+    np.testing.assert_array_equal(np.sort(b[:, 1]), be)
+
+
+def test_rejects_bad_input():
+    good = np.array([[1, 5]], np.uint32)
+    with pytest.raises(ValueError):
+        O.count(np.array([[5, 4]], np.uint32), good)        # inverted query
+    with pytest.raises(ValueError):
+        O.count(good, np.array([[3, 3]], np.uint32))        # empty database interval
+    with pytest.raises(ValueError):
+        O.mc_place(np.array([[95, 105]], np.uint32), [0, 100], [100, 100], 1, 0)  # crosses contig
+
+
+def test_extreme_coordinates():
+    top = 2**32 - 1
+    b = np.array([[top - 5, top], [0, 1], [top - 1, top]], np.uint32)
+    a = np.array([[top - 1, top - 1], [top - 2, top], [top, top], [0, 0], [0, top]], np.uint32)
+    c1, _ = O.count_brute(a, b)
+    c2, _ = O.count(a, b)
+    np.testing.assert_array_equal(c1, c2)
+    np.testing.assert_array_equal(c1, [1, 2, 0, 0, 3])
+
+
+# ------------------------------------------------------------------ Philox and the position map
+
+def test_philox_known_answers():
+    for ctr, key, expect in read_philox_kat():
+        np.testing.assert_array_equal(O.philox(ctr, key), np.array(expect, np.uint32))
+
+
+def test_scale_matches_exact_integer_arithmetic():
+    rng = np.random.default_rng(3)
+    cases = [(0, 1), (2**64 - 1, 1), (2**64 - 1, 2**32), (2**63, 3), (1, 2**33)]
+    for _ in range(2000):
+        cases.append((int(rng.integers(0, 2**63)) * 2 + int(rng.integers(0, 2)),
+                      int(rng.integers(1, 2**32 + 1))))
+    for u, n in cases:
+        assert O.scale_u64(u, n) == (u * n) >> 64
+
+
+def test_mc_place_pinned_by_known_answer():
+    # Interval 0 of shuffle 0 with seed 0 draws Philox(ctr 0, key 0), the first
+    # known-answer vector: x0 = 6627e8d5, x1 = e169c58d.
+    u = (0xE169C58D << 32) | 0x6627E8D5
+    off, ln = [0, 1000], [1000, 5000]
+    for length, contig in ((10, 0), (123, 1), (1000, 0)):
+        start = off[contig] + 7 if length < 1000 else off[contig]
+        a = np.array([[start, start + length]], np.uint32)
+        out = O.mc_place(a, off, ln, seed=0, s=0)
+        expect = off[contig] + ((u * (ln[contig] - length + 1)) >> 64)
+        assert int(out[0, 0]) == expect and int(out[0, 1]) == expect + length
+
+
+def test_mc_place_invariants():
+    genome, a, _ = synth.config3(n_a=5000, n_b=10)
+    co, cl = synth.mc_contig_table(genome)
+    contig_before = np.searchsorted(co, a[:, 0], side="right") - 1
+    for s in (0, 1, 77, 9999):
+        p = O.mc_place(a, co, cl, seed=7, s=s)
+        np.testing.assert_array_equal(p[:, 1] - p[:, 0], a[:, 1] - a[:, 0])   # length kept
+        c = np.searchsorted(co, p[:, 0], side="right") - 1
+        np.testing.assert_array_equal(c, contig_before)                       # contig kept
+        assert (p[:, 1].astype(np.int64) <= co[c].astype(np.int64) + cl[c]).all()  # inside it
+    assert not np.array_equal(O.mc_place(a, co, cl, 7, 0), O.mc_place(a, co, cl, 7, 1))
+
+
+def test_mc_place_uniform_chi_square():
+    # One interval, 20000 shuffles, range 1000: 10 equal bins of offsets.
+    a = np.array([[100, 101]], np.uint32)
+    co, cl = np.array([0], np.uint32), np.array([1000], np.uint32)
+    offs = np.array([int(O.mc_place(a, co, cl, seed=12345, s=s)[0, 0]) for s in range(20000)])
+    hist = np.bincount(offs // 100, minlength=10)
+    chi2 = float((((hist - 2000.0) ** 2) / 2000.0).sum())
+    assert chi2 < 37.0   # chi-square with 9 dof, p about 4e-5
+
+
+def test_mc_fixed_placement_closed_form():
+    # Contigs exactly as long as their interval: every shuffle puts it at the
+    # contig start, so every total equals the count of A moved to contig starts.
+    co = np.array([0, 100, 300], np.uint32)
+    cl = np.array([100, 200, 50], np.uint32)
+    a = np.array([[10, 110 - 10], [150, 350], [320, 330]], np.uint32)
+    a[0] = [0, 100]
+    a[1] = [100, 300]
+    a[2] = [300, 350]
+    b = np.array([[50, 60], [99, 101], [299, 301], [340, 345], [0, 400]], np.uint32)
+    bs, be = O.build(b)
+    totals, obs, k, p = O.mc(a, co, cl, bs, be, seed=5, s_begin=0, s_end=16)
+    _, expect = O.count_brute(a, b)
+    assert (totals == expect).all() and obs == expect
+    assert k == 16 and p == 1.0
+
+
+def test_mc_tally_and_pvalue():
+    genome, a, b = synth.config3(n_a=300, n_b=3000, n_hot=50)
+    co, cl = synth.mc_contig_table(genome)
+    bs, be = O.build(b)
+    totals, obs, k, p = O.mc(a, co, cl, bs, be, seed=7, s_begin=0, s_end=64)
+    _, obs_brute = O.count_brute(a, b)
+    assert obs == obs_brute
+    assert k == int((totals >= obs).sum())
+    assert p == (k + 1) / 65.0 and 1 / 65.0 <= p <= 1.0
+    for s in (0, 13, 63):                                   # each total is a recount
+        _, t = O.count_brute(O.mc_place(a, co, cl, 7, s), b)
+        assert totals[s] == t
+    t_lo, *_ = O.mc(a, co, cl, bs, be, seed=7, s_begin=0, s_end=20)   # resumable by range
+    t_hi, *_ = O.mc(a, co, cl, bs, be, seed=7, s_begin=20, s_end=64)
+    np.testing.assert_array_equal(np.concatenate([t_lo, t_hi]), totals)
+    t_mt, *_ = O.mc(a, co, cl, bs, be, seed=7, s_begin=0, s_end=64, threads=4)
+    np.testing.assert_array_equal(t_mt, totals)
+    # Observed beyond every shuffle: p is the smallest possible value.
+    empty = np.zeros(0, np.uint32)
+    tz, oz, kz, pz = O.mc(a, co, cl, empty, empty, seed=7, s_begin=0, s_end=9)
+    assert (tz == 0).all() and oz == 0 and kz == 9 and pz == 1.0
+
+
+# ------------------------------------------------------------------- planted mistakes
+
+MUTANTS = ["ORACLE_MUTANT_CLOSED", "ORACLE_MUTANT_LAST_LOWER", "ORACLE_MUTANT_PHILOX",
+           "ORACLE_MUTANT_SCALE", "ORACLE_MUTANT_WORD_ORDER", "ORACLE_MUTANT_TALLY"]
+
+
+def _pins_pass(o: oracle.Oracle) -> bool:
+    try:
+        for name in ("containment.txt", "duplicates.txt"):
+            a, b, exp, total = read_count_fixture(name)
+            c, t = o.count_brute(a, b)
+            assert (c == exp).all() and t == total
+            c, t = o.count(a, b)
+            assert (c == exp).all() and t == total
+        for ctr, key, expect in read_philox_kat():
+            assert (o.philox(ctr, key) == np.array(expect, np.uint32)).all()
+        u = (0xE169C58D << 32) | 0x6627E8D5
+        out = o.mc_place(np.array([[7, 17]], np.uint32), [0], [1000], seed=0, s=0)
+        assert int(out[0, 0]) == (u * 991) >> 64
+        for uu, n in ((2**64 - 1, 2**32), (2**63, 3)):
+            assert o.scale_u64(uu, n) == (uu * n) >> 64
+        co = np.array([0], np.uint32)
+        cl = np.array([10], np.uint32)
+        aa = np.array([[0, 10]], np.uint32)
+        bb = np.array([[2, 3]], np.uint32)
+        bs, be = o.build(bb)
+        tot, obs, k, p = o.mc(aa, co, cl, bs, be, seed=1, s_begin=0, s_end=4)
+        assert k == 4 and p == 1.0
+        return True
+    except AssertionError:
+        return False
+
+
+def test_pins_pass_on_the_real_oracle():
+    assert _pins_pass(O)
+
+
+@pytest.mark.parametrize("mutant", MUTANTS)
+def test_mutants_fail_pins(mutant):
+    with tempfile.TemporaryDirectory() as d:
+        path = oracle.build(os.path.join(d, "libmut.so"), defines=(mutant,))
+        assert not _pins_pass(oracle.Oracle(oracle.load(path)))
