@@ -1,0 +1,155 @@
+/*
+ * bits.h -- C ABI of the B300 (sm_103a) Binary Interval Search library.
+ *
+ * Binary Interval Search (BITS; Layer, Skadron, Robins, Hall and Quinlan,
+ * Bioinformatics 2012) counts interval intersections by exclusion: for a
+ * query a and a database B split into independently sorted start and end
+ * arrays B_S and B_E, the number of database intervals meeting a is
+ *     ICount(a) = #(B_S < a.end) - #(B_E <= a.start)           (Algorithm 1)
+ * which equals |B| minus the intervals wholly right of a, minus those wholly
+ * left of a (Sec. 2.2, the sets L and R).  The counting problem sums ICount
+ * over A (Algorithm 2); the Monte-Carlo significance test (Sec. 3.2) recounts
+ * after re-placing A at random many times.
+ *
+ * Conventions shared by every call:
+ *   - Intervals are half-open [start, end) pairs of uint32 on one genome-wide
+ *     coordinate line (contigs already projected by adding their offsets, as
+ *     Sec. 2.3 describes).  An interval set is an array of structures: element
+ *     i is the two consecutive words (start_i, end_i), 8 bytes per interval.
+ *     a and b intersect iff b.start < a.end and b.end > a.start.
+ *   - Database intervals must be non-empty (start < end).  Queries may be
+ *     empty (start == end) and then count the database intervals with
+ *     start < x < end; queries with end < start are invalid.
+ *   - Pointers named d_* are device pointers on the current CUDA device, h_*
+ *     are host pointers.  The caller owns every pointer it passes; the library
+ *     never frees them.  A bits_db owns its own device memory until bits_free.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered; a call that returns host values
+ *     synchronises that stream first.
+ *   - Every call returns a bits_status; on failure bits_last_error() gives a
+ *     message (thread-local).  No call falls back to host computation.
+ */
+#ifndef BITS_H
+#define BITS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bits_db bits_db;
+
+typedef enum bits_status {
+  BITS_OK = 0,
+  BITS_EINVAL = 1,     /* bad argument, or an invalid interval was seen          */
+  BITS_ENOMEM = 2,     /* device allocation failed                               */
+  BITS_ECUDA = 3,      /* CUDA runtime error (message in bits_last_error)        */
+  BITS_EOVERFLOW = 4,  /* a size beyond the supported range                      */
+  BITS_ETIMEOUT = 5,   /* a bounded device-side wait gave up; results invalid    */
+  BITS_ENOTIMPL = 6    /* method not built into this database                    */
+} bits_status;
+
+typedef enum bits_method {
+  BITS_METHOD_AUTO = 0,      /* autotuner picks among the built methods            */
+  BITS_METHOD_SEARCH = 1,    /* shared-memory top tree + per-thread binary search  */
+  BITS_METHOD_RMI = 2,       /* learned index: predict, bounded search, verify     */
+  BITS_METHOD_MERGEPATH = 3  /* sort the queries, co-rank them by merge path       */
+} bits_method;
+
+/* Build options; pass NULL for the defaults (every field 0). */
+typedef struct bits_opts {
+  int32_t method;          /* bits_method the database uses by default           */
+  int32_t rmi_leaves_log2; /* 0: no learned index; else 2^k linear leaves per     */
+                           /* sorted array, k in [1, 22]                          */
+  int32_t top_tree_log2;   /* 0: default 12; samples per array kept in shared    */
+                           /* memory are 2^k - 1, k in [1, 14]                    */
+  int32_t reserved;        /* must be 0                                           */
+} bits_opts;
+
+/*
+ * bits_build_db -- Algorithm 2's set-up: B_S <- starts, B_E <- ends, sort both.
+ *   d_b   device, n intervals as (start, end) uint32 pairs; read only.
+ *   n     number of database intervals, 0 <= n < 2^30 (else BITS_EOVERFLOW).
+ *   out   receives the new database handle (owns B_S, B_E, search tree and
+ *         the optional learned index).
+ * Sorting is the library's own LSD radix sort.  The call synchronises the
+ * stream once (it reads the validation flag): BITS_EINVAL if any interval has
+ * end <= start, in which case *out is left NULL.
+ */
+bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts, void* stream,
+                          bits_db** out);
+
+/*
+ * bits_count -- Algorithm 2's counting loop over Algorithm 1.
+ *   d_a       device, n queries as (start, end) uint32 pairs; read only.
+ *   n         number of queries, n < 2^32.
+ *   d_counts  device uint32[n] receiving ICount(a_i), or NULL to skip.
+ *   d_total   device uint64[1] receiving the sum over all queries.
+ * Asynchronous.  Inverted queries (end < start) count 0 and set the
+ * database's device error word; bits_check reports it as BITS_EINVAL.
+ */
+bits_status bits_count(const bits_db* db, const uint32_t* d_a, uint64_t n, uint32_t* d_counts,
+                       uint64_t* d_total, void* stream);
+
+/* Same as bits_count with an explicit method (for side-by-side comparison). */
+bits_status bits_count_method(const bits_db* db, int32_t method, const uint32_t* d_a,
+                              uint64_t n, uint32_t* d_counts, uint64_t* d_total, void* stream);
+
+/*
+ * bits_mc -- Monte-Carlo significance test of Sec. 3.2.  Each shuffle s in
+ * [shuffle_begin, shuffle_end) re-places every query interval uniformly inside
+ * its own contig with its length kept, and recounts it against the fixed
+ * database.  Interval i of shuffle s draws Philox4x32-10 with counter
+ * (i, s, 0, 0) and key (seed & 0xffffffff, seed >> 32); with u = x1*2^32 + x0
+ * its new start is off[c] + floor(u * (len[c] - len_i + 1) / 2^64).
+ *   d_contig_off, d_contig_len  device uint32[n_contigs], the contig table on
+ *                               the same coordinate line (offsets ascending).
+ *   d_totals    device uint64[shuffle_end - shuffle_begin], per-shuffle totals.
+ *   h_observed  host, total of the unshuffled queries (nullable).
+ *   h_k_ge      host, #{s : total_s >= observed} (nullable).
+ *   h_pvalue    host, (k_ge + 1) / (N + 1) in IEEE double (nullable).
+ * method: BITS_METHOD_SEARCH or BITS_METHOD_RMI (AUTO picks).  Synchronises the
+ * stream.  BITS_EINVAL if a query is inverted, lies before the first contig or
+ * crosses its contig's end.  Work of one call runs as one persistent launch,
+ * replayed from a cached CUDA graph when the same arguments repeat.
+ */
+bits_status bits_mc(const bits_db* db, int32_t method, const uint32_t* d_a, uint64_t n,
+                    const uint32_t* d_contig_off, const uint32_t* d_contig_len,
+                    uint32_t n_contigs, uint64_t seed, uint32_t shuffle_begin,
+                    uint32_t shuffle_end, uint64_t* d_totals, uint64_t* h_observed,
+                    uint64_t* h_k_ge, double* h_pvalue, void* stream);
+
+/*
+ * bits_count_matrix -- all-pairs screen of Sec. 3.3: M[i][j] = total(A_i, B_j).
+ *   dbs      host array of n_db database handles (all on this device).
+ *   d_as     host array of n_sets device pointers to query sets.
+ *   n_as     host array of n_sets query-set sizes.
+ *   d_matrix device uint64[n_sets][n_db], row-major.
+ * One persistent launch over (query chunk, database) work units ordered by
+ * cost; asynchronous.
+ */
+bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
+                              const uint32_t* const* d_as, const uint64_t* n_as, uint32_t n_sets,
+                              uint64_t* d_matrix, void* stream);
+
+/* Read-only views of the database (sorted starts, sorted ends, size). */
+bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_t** d_be,
+                         uint64_t* n, int32_t* has_rmi);
+
+/* Synchronise `stream`, then return and clear the database's device error word. */
+bits_status bits_check(const bits_db* db, void* stream);
+
+/* Release a database (NULL-safe).  Stream-ordered on the stream it was built on. */
+void bits_free(bits_db* db);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* bits_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t bits_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BITS_H */

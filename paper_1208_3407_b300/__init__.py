@@ -1,0 +1,171 @@
+"""Binary Interval Search (BITS) on one NVIDIA B300 -- Python binding.
+
+A thin layer over the C ABI of ``libbits_b300.so`` (include/bits.h): it
+checks tensor shapes and devices, passes raw pointers and the current torch
+stream, and turns status codes into exceptions.  All computation runs in the
+library's CUDA kernels; PyTorch only provides device memory and streams.
+
+Interval sets are CUDA tensors of shape ``(n, 2)`` and dtype ``uint32`` (or
+``int32`` holding the same bits), rows ``[start, end)`` on one genome-wide
+coordinate line.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import (METHOD_AUTO, METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, BitsError,
+                   LIB_PATH)
+
+__all__ = ["Database", "count_matrix", "kernel_launches", "BitsError", "METHOD_AUTO",
+           "METHOD_SEARCH", "METHOD_RMI", "METHOD_MERGEPATH", "LIB_PATH", "device_view"]
+
+_U32 = (torch.uint32, torch.int32)
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _intervals(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype not in _U32 or x.dim() != 2 or x.shape[1] != 2:
+        raise TypeError(f"{name} must be a (n, 2) uint32/int32 tensor")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return x
+
+
+def _u32_vec(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype not in _U32 or x.dim() != 1:
+        raise TypeError(f"{name} must be a 1-D uint32/int32 CUDA tensor")
+    return x.contiguous()
+
+
+class _CAI:
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def device_view(ptr: int, n: int, dtype: str = "<u4") -> torch.Tensor:
+    """A torch view of library-owned device memory (no copy)."""
+    if n == 0:
+        return torch.empty(0, dtype=torch.uint32, device="cuda")
+    return torch.as_tensor(_CAI(ptr, n, dtype), device="cuda")
+
+
+class Database:
+    """A BITS database: the sorted start and end arrays of B (Algorithm 2)."""
+
+    def __init__(self, b: torch.Tensor, *, method: int = 0, rmi_leaves_log2: int = 0,
+                 top_tree_log2: int = 0, stream=None):
+        b = _intervals(b, "b")
+        self._lib = _lib.load()
+        self.device = b.device
+        opts = _lib.Opts(method, rmi_leaves_log2, top_tree_log2, 0)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self._lib.bits_build_db(b.data_ptr() if b.numel() else None, b.shape[0],
+                                         C.byref(opts), _stream_ptr(stream), C.byref(h))
+        _lib.check(st, "bits_build_db")
+        self._h = h
+        self.n = int(b.shape[0])
+        bs, be, n, rmi = C.c_void_p(), C.c_void_p(), C.c_uint64(), C.c_int32()
+        _lib.check(self._lib.bits_db_info(h, C.byref(bs), C.byref(be), C.byref(n), C.byref(rmi)),
+                   "bits_db_info")
+        self._bs, self._be, self.has_rmi = bs.value or 0, be.value or 0, bool(rmi.value)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def sorted_arrays(self):
+        """(B_S, B_E) as uint32 views of the database's own device memory."""
+        return device_view(self._bs, self.n), device_view(self._be, self.n)
+
+    def count(self, a: torch.Tensor, *, counts: bool | torch.Tensor = True, method: int | None = None,
+              total: torch.Tensor | None = None, stream=None, check: bool = True):
+        """Per-query counts (uint32, or None) and the uint64 total (1-element tensor)."""
+        a = _intervals(a, "a")
+        n = int(a.shape[0])
+        if isinstance(counts, torch.Tensor):
+            out = counts
+            if out.dtype not in _U32 or out.numel() < n or not out.is_contiguous():
+                raise TypeError("counts must be a contiguous uint32 tensor of >= n elements")
+        else:
+            out = torch.empty(n, dtype=torch.uint32, device=a.device) if counts else None
+        if total is None:
+            total = torch.empty(1, dtype=torch.uint64, device=a.device)
+        sp = _stream_ptr(stream)
+        cp = out.data_ptr() if (out is not None and n) else None
+        ap = a.data_ptr() if n else None
+        if method is None:
+            st = self._lib.bits_count(self._h, ap, n, cp, total.data_ptr(), sp)
+        else:
+            st = self._lib.bits_count_method(self._h, method, ap, n, cp, total.data_ptr(), sp)
+        _lib.check(st, "bits_count")
+        if check:
+            _lib.check(self._lib.bits_check(self._h, sp), "bits_count (device check)")
+        return out, total
+
+    def check(self, stream=None):
+        _lib.check(self._lib.bits_check(self._h, _stream_ptr(stream)), "bits_check")
+
+    def mc(self, a: torch.Tensor, contig_off: torch.Tensor, contig_len: torch.Tensor, *, seed: int,
+           shuffle_begin: int = 0, shuffle_end: int, method: int = METHOD_AUTO,
+           totals: torch.Tensor | None = None, stream=None):
+        """Monte-Carlo test (Sec. 3.2): (totals, observed, k_ge, p-value)."""
+        a = _intervals(a, "a")
+        co = _u32_vec(contig_off, "contig_off")
+        cl = _u32_vec(contig_len, "contig_len")
+        if co.numel() != cl.numel():
+            raise ValueError("contig_off and contig_len differ in length")
+        nsh = shuffle_end - shuffle_begin
+        if totals is None:
+            totals = torch.empty(max(nsh, 0), dtype=torch.uint64, device=a.device)
+        obs, k, p = C.c_uint64(), C.c_uint64(), C.c_double()
+        n = int(a.shape[0])
+        st = self._lib.bits_mc(self._h, method, a.data_ptr() if n else None, n, co.data_ptr(),
+                               cl.data_ptr(), co.numel(), seed, shuffle_begin, shuffle_end,
+                               totals.data_ptr() if nsh > 0 else None, C.byref(obs), C.byref(k),
+                               C.byref(p), _stream_ptr(stream))
+        _lib.check(st, "bits_mc")
+        return totals, obs.value, k.value, p.value
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.bits_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def count_matrix(dbs, a_sets, *, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """M[i][j] = total(A_i, B_j) for query sets A_i and databases B_j (uint64)."""
+    lib = _lib.load()
+    a_sets = [_intervals(a, f"a_sets[{i}]") for i, a in enumerate(a_sets)]
+    n_db, n_sets = len(dbs), len(a_sets)
+    dev = a_sets[0].device if a_sets else torch.device("cuda")
+    if out is None:
+        out = torch.empty((n_sets, n_db), dtype=torch.uint64, device=dev)
+    hs = (C.c_void_p * max(1, n_db))(*[d._h.value for d in dbs])
+    ps = (C.c_void_p * max(1, n_sets))(*[a.data_ptr() if a.shape[0] else None for a in a_sets])
+    ns = (C.c_uint64 * max(1, n_sets))(*[int(a.shape[0]) for a in a_sets])
+    st = lib.bits_count_matrix(hs, n_db, ps, ns, n_sets, out.data_ptr() if out.numel() else None,
+                               _stream_ptr(stream))
+    _lib.check(st, "bits_count_matrix")
+    return out
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(_lib.load().bits_kernel_launches())

@@ -1,0 +1,13 @@
+// All-pairs count matrix (allpairs.cu).
+#pragma once
+
+#include "common.cuh"
+#include "db.cuh"
+
+namespace bits {
+
+bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
+                             const uint32_t* const* d_as, const uint64_t* n_as, uint32_t n_sets,
+                             uint64_t* d_matrix, cudaStream_t st);
+
+}  // namespace bits

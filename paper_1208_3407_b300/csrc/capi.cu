@@ -1,0 +1,322 @@
+// C ABI entry points (include/bits.h) and the host runtime around them:
+// database construction and ownership, argument checking, method dispatch,
+// error reporting and the launch counter.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "count.cuh"
+#include "db.cuh"
+#include "mc.cuh"
+#include "radix_sort.cuh"
+#include "rmi.cuh"
+#include "allpairs.cuh"
+#include "mergepath.cuh"
+
+namespace bits {
+namespace {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+std::mutex g_sm_mu;
+std::vector<int> g_sm_count;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+void count_launch(uint32_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int sm_count() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_sm_mu);
+  if ((int)g_sm_count.size() <= dev) g_sm_count.resize(dev + 1, 0);
+  if (g_sm_count[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    g_sm_count[dev] = v > 0 ? v : 1;
+  }
+  return g_sm_count[dev];
+}
+
+bits_status cuda_status(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? BITS_ENOMEM : BITS_ECUDA;
+}
+
+bits_status read_device_error(const bits_db* db, cudaStream_t st, bool clear) {
+  uint32_t h = 0;
+  BITS_CUDA_TRY(cudaMemcpyAsync(&h, db->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  BITS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (clear && h) BITS_CUDA_TRY(cudaMemsetAsync(db->err, 0, sizeof(uint32_t), st));
+  if (h & DEV_ERR_TIMEOUT) {
+    set_error("a bounded device-side wait timed out; results are invalid");
+    return BITS_ETIMEOUT;
+  }
+  if (h & DEV_ERR_INVALID) {
+    set_error("an invalid interval was seen (query end < start, or outside its contig)");
+    return BITS_EINVAL;
+  }
+  return BITS_OK;
+}
+
+// Bucket size 2^k so that the buckets fit the 2^t - 1 tree slots.
+static int bucket_log2_for(uint32_t n, int t) {
+  const uint64_t slots = (1ull << t) - 1;
+  int k = 0;
+  while (((uint64_t)n + (1ull << k) - 1) >> k > slots) ++k;
+  return k;
+}
+
+}  // namespace bits
+
+using namespace bits;
+
+extern "C" {
+
+const char* bits_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t bits_kernel_launches(void) { return g_launches.load(); }
+
+bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts, void* stream,
+                          bits_db** out) {
+  if (!out) {
+    set_error("bits_build_db: out is NULL");
+    return BITS_EINVAL;
+  }
+  *out = nullptr;
+  if (n && !d_b) {
+    set_error("bits_build_db: d_b is NULL");
+    return BITS_EINVAL;
+  }
+  if (n >= (1ull << 30)) {
+    set_error("bits_build_db: at most 2^30 - 1 database intervals are supported");
+    return BITS_EOVERFLOW;
+  }
+  if (reinterpret_cast<uintptr_t>(d_b) % 8) {
+    set_error("bits_build_db: d_b must be 8-byte aligned");
+    return BITS_EINVAL;
+  }
+  bits_opts o{};
+  if (opts) o = *opts;
+  const int t = o.top_tree_log2 ? o.top_tree_log2 : 12;
+  if (t < 1 || t > 14 || o.rmi_leaves_log2 < 0 || o.rmi_leaves_log2 > 22 || o.reserved != 0 ||
+      o.method < 0 || o.method > BITS_METHOD_MERGEPATH) {
+    set_error("bits_build_db: option out of range");
+    return BITS_EINVAL;
+  }
+  if (o.method == BITS_METHOD_RMI && o.rmi_leaves_log2 == 0) {
+    set_error("bits_build_db: method RMI needs rmi_leaves_log2 > 0");
+    return BITS_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t nn = (uint32_t)n;
+
+  auto db = std::make_unique<bits_db>();
+  BITS_CUDA_TRY(cudaGetDevice(&db->device));
+  db->n = nn;
+  db->tree_log2 = t;
+  db->bucket_log2 = bucket_log2_for(nn, t);
+  db->method = o.method ? o.method : (o.rmi_leaves_log2 ? BITS_METHOD_AUTO : BITS_METHOD_SEARCH);
+  db->has_rmi = o.rmi_leaves_log2 > 0;
+
+  // One allocation: bs | be | tree | err | rmi leaves (starts) | rmi leaves (ends).
+  const size_t off_bs = 0;
+  const size_t off_be = align_up(off_bs + sizeof(uint32_t) * (size_t)std::max<uint32_t>(nn, 1), 256);
+  const size_t off_tree = align_up(off_be + sizeof(uint32_t) * (size_t)std::max<uint32_t>(nn, 1), 256);
+  const size_t off_err = align_up(off_tree + sizeof(uint32_t) * (2ull << t), 256);
+  size_t off_rmi = align_up(off_err + 256, 256);
+  const size_t leaves = db->has_rmi ? (1ull << o.rmi_leaves_log2) : 0;
+  const size_t total = off_rmi + 2 * leaves * sizeof(bits_rmi_leaf);
+  void* block = nullptr;
+  BITS_CUDA_TRY(cudaMalloc(&block, total));
+  db->block = block;
+  db->block_bytes = total;
+  char* base = static_cast<char*>(block);
+  db->bs = reinterpret_cast<uint32_t*>(base + off_bs);
+  db->be = reinterpret_cast<uint32_t*>(base + off_be);
+  db->tree = reinterpret_cast<uint32_t*>(base + off_tree);
+  db->err = reinterpret_cast<uint32_t*>(base + off_err);
+  if (db->has_rmi) {
+    db->rmi[0].leaves_log2 = db->rmi[1].leaves_log2 = o.rmi_leaves_log2;
+    db->rmi[0].leaves = reinterpret_cast<bits_rmi_leaf*>(base + off_rmi);
+    db->rmi[1].leaves = db->rmi[0].leaves + leaves;
+  }
+  auto fail = [&](bits_status s) {
+    cudaStreamSynchronize(st);
+    cudaFree(block);
+    return s;
+  };
+  if (cudaMemsetAsync(db->err, 0, sizeof(uint32_t), st) != cudaSuccess)
+    return fail(cuda_status(cudaGetLastError(), "cudaMemsetAsync"));
+
+  if (nn) {
+    RadixScratch ws{};
+    const size_t sw = radix_status_words(nn);
+    const size_t scratch_bytes = 2 * align_up(sizeof(uint32_t) * nn, 256) +
+                                 align_up(sizeof(uint32_t) * 2048, 256) +
+                                 align_up(sizeof(uint32_t) * sw * 8, 256) + 256;
+    void* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, st);
+    if (e != cudaSuccess) return fail(cuda_status(e, "cudaMallocAsync(sort scratch)"));
+    char* sb = static_cast<char*>(scratch);
+    ws.tmp_s = reinterpret_cast<uint32_t*>(sb);
+    sb += align_up(sizeof(uint32_t) * nn, 256);
+    ws.tmp_e = reinterpret_cast<uint32_t*>(sb);
+    sb += align_up(sizeof(uint32_t) * nn, 256);
+    ws.hist = reinterpret_cast<uint32_t*>(sb);
+    sb += align_up(sizeof(uint32_t) * 2048, 256);
+    ws.status = reinterpret_cast<uint32_t*>(sb);
+    sb += align_up(sizeof(uint32_t) * sw * 8, 256);
+    ws.tickets = reinterpret_cast<uint32_t*>(sb);
+    bits_status s = radix_sort_intervals(reinterpret_cast<const uint2*>(d_b), nn, db->bs, db->be,
+                                         db->err, ws, st);
+    cudaFreeAsync(scratch, st);
+    if (s != BITS_OK) return fail(s);
+  }
+  bits_status s = sample_top_tree(db->bs, db->be, nn, t, db->bucket_log2, db->tree, st);
+  if (s != BITS_OK) return fail(s);
+  if (db->has_rmi) {
+    for (int a = 0; a < 2; ++a) {
+      s = rmi_build(a ? db->be : db->bs, nn, db->rmi[a], st);
+      if (s != BITS_OK) return fail(s);
+    }
+  }
+  s = read_device_error(db.get(), st, false);
+  if (s != BITS_OK) return fail(s);
+  *out = db.release();
+  return BITS_OK;
+}
+
+bits_status bits_count_method(const bits_db* db, int32_t method, const uint32_t* d_a, uint64_t n,
+                              uint32_t* d_counts, uint64_t* d_total, void* stream) {
+  if (!db || !d_total || (n && !d_a)) {
+    set_error("bits_count: NULL argument");
+    return BITS_EINVAL;
+  }
+  if (n >= (1ull << 32)) {
+    set_error("bits_count: at most 2^32 - 1 queries per call");
+    return BITS_EOVERFLOW;
+  }
+  if (reinterpret_cast<uintptr_t>(d_a) % 8 || reinterpret_cast<uintptr_t>(d_counts) % 4 ||
+      reinterpret_cast<uintptr_t>(d_total) % 8) {
+    set_error("bits_count: misaligned pointer (queries 8 B, counts 4 B, total 8 B)");
+    return BITS_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (method == BITS_METHOD_AUTO) method = choose_count_method(db, (uint32_t)n);
+  switch (method) {
+    case BITS_METHOD_SEARCH:
+      return launch_count_search(db, d_a, (uint32_t)n, d_counts, d_total, st);
+    case BITS_METHOD_RMI:
+      if (!db->has_rmi) {
+        set_error("bits_count: database was built without a learned index");
+        return BITS_ENOTIMPL;
+      }
+      return launch_count_rmi(db, d_a, (uint32_t)n, d_counts, d_total, st);
+    case BITS_METHOD_MERGEPATH:
+      return launch_count_mergepath(db, d_a, (uint32_t)n, d_counts, d_total, st);
+    default:
+      set_error("bits_count: unknown method");
+      return BITS_EINVAL;
+  }
+}
+
+bits_status bits_count(const bits_db* db, const uint32_t* d_a, uint64_t n, uint32_t* d_counts,
+                       uint64_t* d_total, void* stream) {
+  if (!db) {
+    set_error("bits_count: db is NULL");
+    return BITS_EINVAL;
+  }
+  return bits_count_method(db, db->method, d_a, n, d_counts, d_total, stream);
+}
+
+bits_status bits_mc(const bits_db* db, int32_t method, const uint32_t* d_a, uint64_t n,
+                    const uint32_t* d_contig_off, const uint32_t* d_contig_len, uint32_t n_contigs,
+                    uint64_t seed, uint32_t shuffle_begin, uint32_t shuffle_end,
+                    uint64_t* d_totals, uint64_t* h_observed, uint64_t* h_k_ge, double* h_pvalue,
+                    void* stream) {
+  if (!db || (n && !d_a) || !d_contig_off || !d_contig_len || n_contigs == 0 ||
+      shuffle_end < shuffle_begin || (shuffle_end > shuffle_begin && !d_totals)) {
+    set_error("bits_mc: bad argument");
+    return BITS_EINVAL;
+  }
+  if (n >= (1ull << 32)) {
+    set_error("bits_mc: at most 2^32 - 1 queries");
+    return BITS_EOVERFLOW;
+  }
+  if (method == BITS_METHOD_AUTO) method = db->has_rmi ? BITS_METHOD_RMI : BITS_METHOD_SEARCH;
+  if (method == BITS_METHOD_RMI && !db->has_rmi) {
+    set_error("bits_mc: database was built without a learned index");
+    return BITS_ENOTIMPL;
+  }
+  if (method != BITS_METHOD_SEARCH && method != BITS_METHOD_RMI) {
+    set_error("bits_mc: method must be SEARCH or RMI");
+    return BITS_EINVAL;
+  }
+  return run_mc(const_cast<bits_db*>(db), method, d_a, (uint32_t)n, d_contig_off, d_contig_len,
+                n_contigs, seed, shuffle_begin, shuffle_end, d_totals, h_observed, h_k_ge,
+                h_pvalue, static_cast<cudaStream_t>(stream));
+}
+
+bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
+                              const uint32_t* const* d_as, const uint64_t* n_as, uint32_t n_sets,
+                              uint64_t* d_matrix, void* stream) {
+  if ((n_db && !dbs) || (n_sets && (!d_as || !n_as)) || (n_db && n_sets && !d_matrix)) {
+    set_error("bits_count_matrix: NULL argument");
+    return BITS_EINVAL;
+  }
+  for (uint32_t j = 0; j < n_db; ++j)
+    if (!dbs[j]) {
+      set_error("bits_count_matrix: NULL database handle");
+      return BITS_EINVAL;
+    }
+  for (uint32_t i = 0; i < n_sets; ++i) {
+    if (n_as[i] >= (1ull << 32)) {
+      set_error("bits_count_matrix: a query set has 2^32 or more intervals");
+      return BITS_EOVERFLOW;
+    }
+    if (n_as[i] && (!d_as[i] || reinterpret_cast<uintptr_t>(d_as[i]) % 8)) {
+      set_error("bits_count_matrix: query set pointer NULL or not 8-byte aligned");
+      return BITS_EINVAL;
+    }
+  }
+  return run_count_matrix(dbs, n_db, d_as, n_as, n_sets, d_matrix,
+                          static_cast<cudaStream_t>(stream));
+}
+
+bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_t** d_be,
+                         uint64_t* n, int32_t* has_rmi) {
+  if (!db) {
+    set_error("bits_db_info: db is NULL");
+    return BITS_EINVAL;
+  }
+  if (d_bs) *d_bs = db->bs;
+  if (d_be) *d_be = db->be;
+  if (n) *n = db->n;
+  if (has_rmi) *has_rmi = db->has_rmi ? 1 : 0;
+  return BITS_OK;
+}
+
+bits_status bits_check(const bits_db* db, void* stream) {
+  if (!db) {
+    set_error("bits_check: db is NULL");
+    return BITS_EINVAL;
+  }
+  return read_device_error(db, static_cast<cudaStream_t>(stream), true);
+}
+
+void bits_free(bits_db* db) {
+  if (!db) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != db->device) cudaSetDevice(db->device);
+  release_mc_graphs(db);
+  cudaFree(db->block);
+  if (prev != db->device) cudaSetDevice(prev);
+  delete db;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// Shared definitions of the BITS CUDA library (device + host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+
+#include "../../include/bits.h"
+
+namespace bits {
+
+// Bits OR-ed into a database's device error word.
+enum : uint32_t {
+  DEV_ERR_INVALID = 1u,   // an interval violated the input rules
+  DEV_ERR_TIMEOUT = 2u,   // a bounded spin-wait gave up
+};
+
+// Iterations a spin-wait may take (each sleeps ~100-200 ns) before it gives
+// up and reports DEV_ERR_TIMEOUT: about one second of waiting.
+constexpr uint32_t kSpinLimit = 1u << 23;
+
+constexpr uint32_t kU32Max = 0xFFFFFFFFu;
+
+// Host helpers (defined in capi.cu).
+void set_error(const std::string& msg);
+void count_launch(uint32_t k = 1);
+int sm_count();
+bits_status cuda_status(cudaError_t e, const char* what);
+
+#define BITS_CUDA_TRY(expr)                                         \
+  do {                                                              \
+    cudaError_t _e = (expr);                                        \
+    if (_e != cudaSuccess) return ::bits::cuda_status(_e, #expr);   \
+  } while (0)
+
+#define BITS_LAUNCH_CHECK(what)                                     \
+  do {                                                              \
+    ::bits::count_launch();                                         \
+    cudaError_t _e = cudaGetLastError();                            \
+    if (_e != cudaSuccess) return ::bits::cuda_status(_e, what);    \
+  } while (0)
+
+__device__ __forceinline__ void set_dev_error(uint32_t* err, uint32_t bit) {
+  if (err) atomicOr(err, bit);
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// 64-bit block sum; result valid in thread 0.  `red` holds >= 32 entries.
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
+                                                            unsigned long long* red) {
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  const unsigned w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane_id() == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane_id() < nw ? red[lane_id()] : 0ull;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  }
+  return v;
+}
+
+}  // namespace bits

@@ -1,0 +1,80 @@
+"""The C-ABI library loads and exports every symbol include/bits.h declares.
+
+No compute call here: these run without a GPU.  Argument checks that
+return before touching CUDA are exercised too.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bits.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bits_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1208_3407_b300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_1208_3407_b300 import build
+        build.build()
+    return _lib.load()
+
+
+def test_header_lists_the_binding_exports():
+    from paper_1208_3407_b300 import _lib
+    assert _declared() == sorted(_lib.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_host_side_argument_checks(lib):
+    from paper_1208_3407_b300 import _lib
+    assert lib.bits_build_db(None, 0, None, None, None) == _lib.BITS_EINVAL
+    h = C.c_void_p()
+    assert lib.bits_build_db(None, 5, None, None, C.byref(h)) == _lib.BITS_EINVAL
+    assert h.value is None
+    assert lib.bits_build_db(C.c_void_p(256), 1 << 30, None, None, C.byref(h)) == _lib.BITS_EOVERFLOW
+    assert lib.bits_build_db(C.c_void_p(260), 4, None, None, C.byref(h)) == _lib.BITS_EINVAL
+    assert b"aligned" in lib.bits_last_error()
+    bad = _lib.Opts(0, 0, 15, 0)
+    assert lib.bits_build_db(C.c_void_p(256), 4, C.byref(bad), None, C.byref(h)) == _lib.BITS_EINVAL
+    rmi_without_leaves = _lib.Opts(_lib.METHOD_RMI, 0, 0, 0)
+    assert lib.bits_build_db(C.c_void_p(256), 4, C.byref(rmi_without_leaves), None,
+                             C.byref(h)) == _lib.BITS_EINVAL
+    assert lib.bits_count(None, None, 0, None, None, None) == _lib.BITS_EINVAL
+    assert lib.bits_check(None, None) == _lib.BITS_EINVAL
+    assert lib.bits_db_info(None, None, None, None, None) == _lib.BITS_EINVAL
+    assert lib.bits_mc(None, 0, None, 0, None, None, 0, 0, 0, 0, None, None, None, None,
+                       None) == _lib.BITS_EINVAL
+    assert lib.bits_count_matrix(None, 1, None, None, 0, None, None) == _lib.BITS_EINVAL
+    lib.bits_free(None)
+    assert lib.bits_kernel_launches() == 0
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_1208_3407_b300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        _lib.load()
+
+
+def test_package_does_not_import_oracle():
+    import sys
+    import subprocess
+    code = ("import sys, paper_1208_3407_b300, paper_1208_3407_b300._lib; "
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "False"
