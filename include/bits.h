@@ -133,6 +133,31 @@ bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
                               const uint32_t* const* d_as, const uint64_t* n_as, uint32_t n_sets,
                               uint64_t* d_matrix, void* stream);
 
+/*
+ * bits_sort_intervals_noalloc -- the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory: code whose device
+ * memory is entirely owned by another allocator (a framework's caching pool
+ * that reserves the GPU up front), serving loops that fix their memory plan
+ * at start-up, and callers that cannot afford cudaMalloc's implicit
+ * synchronisation.  It sorts the start words and the end words of n
+ * intervals into d_bs and d_be -- the same arrays bits_build_db builds -- and
+ * allocates nothing: its scratch (about 2.4 MB) is a fixed array inside the
+ * library that every GPU loading the library holds until the process exits.
+ *   d_b    device, n (start, end) uint32 pairs, 8-byte aligned; read only.
+ *   n      0 <= n <= BITS_NOALLOC_MAX_INTERVALS, else BITS_EOVERFLOW.
+ *   d_bs   device uint32[n], receives the sorted starts (caller-owned).
+ *   d_be   device uint32[n], receives the sorted ends (caller-owned).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls on a device share the one scratch array: calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialised
+ * by the caller.  Synchronises `stream`; BITS_EINVAL if an interval has
+ * end <= start.
+ */
+#define BITS_NOALLOC_MAX_INTERVALS 262144u
+bits_status bits_sort_intervals_noalloc(const uint32_t* d_b, uint64_t n, uint32_t* d_bs,
+                                        uint32_t* d_be, void* stream);
+
 /* Read-only views of the database (sorted starts, sorted ends, size). */
 bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_t** d_be,
                          uint64_t* n, int32_t* has_rmi);
