@@ -62,8 +62,9 @@ typedef struct bits_opts {
   int32_t method;          /* bits_method the database uses by default           */
   int32_t rmi_leaves_log2; /* 0: no learned index; else 2^k linear leaves per     */
                            /* sorted array, k in [1, 22]                          */
-  int32_t top_tree_log2;   /* 0: default 12; samples per array kept in shared    */
-                           /* memory are 2^k - 1, k in [1, 14]                    */
+  int32_t top_tree_log2;   /* 0: default 13; the top level of each array's        */
+                           /* 16-ary search tree kept in shared memory holds at   */
+                           /* most 2^k - 1 keys, k in [2, 14]                     */
   int32_t reserved;        /* must be 0                                           */
 } bits_opts;
 
@@ -161,6 +162,22 @@ bits_status bits_sort_intervals_noalloc(const uint32_t* d_b, uint64_t n, uint32_
 /* Read-only views of the database (sorted starts, sorted ends, size). */
 bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_t** d_be,
                          uint64_t* n, int32_t* has_rmi);
+
+/*
+ * bits_db_rmi -- the learned index of one sorted array (which = 0: starts,
+ * 1: ends), for inspection.  The leaf table is device memory owned by the
+ * database: n_leaves records of 32 bytes, each
+ *     uint32 base_key, uint32 lo, float slope, float icpt,
+ *     int32 err_lo, int32 err_hi, uint32 hi, uint32 reserved
+ * (leaf l owns ranks [lo, hi) of the sorted array and predicts the rank of a
+ * key k as lo + round(slope * (k - base_key) + icpt), clamped, with the true
+ * rank inside [prediction + err_lo, prediction + err_hi]).  The root maps k
+ * to leaf floor(root_slope * k + root_icpt), clamped to [0, n_leaves).
+ * The learned index is not in the paper; it narrows each BSearch of
+ * Algorithm 1 before an exact search finishes it.  BITS_ENOTIMPL without one.
+ */
+bits_status bits_db_rmi(const bits_db* db, int32_t which, const void** d_leaves,
+                        uint32_t* n_leaves, float* root_slope, float* root_icpt);
 
 /* Synchronise `stream`, then return and clear the database's device error word. */
 bits_status bits_check(const bits_db* db, void* stream);

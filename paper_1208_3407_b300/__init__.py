@@ -88,6 +88,17 @@ class Database:
         """(B_S, B_E) as uint32 views of the database's own device memory."""
         return device_view(self._bs, self.n), device_view(self._be, self.n)
 
+    def rmi(self, which: int = 0):
+        """Learned index of the starts (0) or ends (1): (leaf table view, root slope, root icpt).
+
+        The view is int32 [n_leaves, 8] over the database's own device memory:
+        base_key, lo, slope bits, icpt bits, err_lo, err_hi, hi, reserved.
+        """
+        p, nl, ra, rb = C.c_void_p(), C.c_uint32(), C.c_float(), C.c_float()
+        _lib.check(self._lib.bits_db_rmi(self._h, which, C.byref(p), C.byref(nl), C.byref(ra),
+                                         C.byref(rb)), "bits_db_rmi")
+        return device_view(p.value, nl.value * 8, "<i4").view(nl.value, 8), ra.value, rb.value
+
     def count(self, a: torch.Tensor, *, counts: bool | torch.Tensor = True, method: int | None = None,
               total: torch.Tensor | None = None, stream=None, check: bool = True):
         """Per-query counts (uint32, or None) and the uint64 total (1-element tensor)."""

@@ -27,6 +27,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 void count_launch(uint32_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void uncount_launch(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 
 int sm_count() {
   int dev = 0;
@@ -62,14 +63,6 @@ bits_status read_device_error(const bits_db* db, cudaStream_t st, bool clear) {
   return BITS_OK;
 }
 
-// Bucket size 2^k so that the buckets fit the 2^t - 1 tree slots.
-static int bucket_log2_for(uint32_t n, int t) {
-  const uint64_t slots = (1ull << t) - 1;
-  int k = 0;
-  while (((uint64_t)n + (1ull << k) - 1) >> k > slots) ++k;
-  return k;
-}
-
 }  // namespace bits
 
 using namespace bits;
@@ -101,8 +94,8 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   }
   bits_opts o{};
   if (opts) o = *opts;
-  const int t = o.top_tree_log2 ? o.top_tree_log2 : 12;
-  if (t < 1 || t > 14 || o.rmi_leaves_log2 < 0 || o.rmi_leaves_log2 > 22 || o.reserved != 0 ||
+  const int t = o.top_tree_log2 ? o.top_tree_log2 : 13;
+  if (t < 2 || t > 14 || o.rmi_leaves_log2 < 0 || o.rmi_leaves_log2 > 22 || o.reserved != 0 ||
       o.method < 0 || o.method > BITS_METHOD_MERGEPATH) {
     set_error("bits_build_db: option out of range");
     return BITS_EINVAL;
@@ -117,17 +110,18 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   auto db = std::make_unique<bits_db>();
   BITS_CUDA_TRY(cudaGetDevice(&db->device));
   db->n = nn;
-  db->tree_log2 = t;
-  db->bucket_log2 = bucket_log2_for(nn, t);
+  plan_levels(nn, t, db->plan);
   db->method = o.method ? o.method : (o.rmi_leaves_log2 ? BITS_METHOD_AUTO : BITS_METHOD_SEARCH);
   db->has_rmi = o.rmi_leaves_log2 > 0;
 
-  // One allocation: bs | be | tree | err | rmi leaves (starts) | rmi leaves (ends).
+  // One allocation: bs | be | levels (both arrays) | top images | err | rmi leaves x 2.
+  const size_t n16 = std::max<uint32_t>(round16(nn), 16);
   const size_t off_bs = 0;
-  const size_t off_be = align_up(off_bs + sizeof(uint32_t) * (size_t)std::max<uint32_t>(nn, 1), 256);
-  const size_t off_tree = align_up(off_be + sizeof(uint32_t) * (size_t)std::max<uint32_t>(nn, 1), 256);
-  const size_t off_err = align_up(off_tree + sizeof(uint32_t) * (2ull << t), 256);
-  size_t off_rmi = align_up(off_err + 256, 256);
+  const size_t off_be = align_up(off_bs + sizeof(uint32_t) * n16, 256);
+  const size_t off_lv = align_up(off_be + sizeof(uint32_t) * n16, 256);
+  const size_t off_top = align_up(off_lv + sizeof(uint32_t) * 2 * db->plan.level_words, 256);
+  const size_t off_err = align_up(off_top + sizeof(uint32_t) * 2 * db->plan.top_size, 256);
+  const size_t off_rmi = align_up(off_err + 256, 256);
   const size_t leaves = db->has_rmi ? (1ull << o.rmi_leaves_log2) : 0;
   const size_t total = off_rmi + 2 * leaves * sizeof(bits_rmi_leaf);
   void* block = nullptr;
@@ -137,7 +131,8 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   char* base = static_cast<char*>(block);
   db->bs = reinterpret_cast<uint32_t*>(base + off_bs);
   db->be = reinterpret_cast<uint32_t*>(base + off_be);
-  db->tree = reinterpret_cast<uint32_t*>(base + off_tree);
+  db->levels = reinterpret_cast<uint32_t*>(base + off_lv);
+  db->top = reinterpret_cast<uint32_t*>(base + off_top);
   db->err = reinterpret_cast<uint32_t*>(base + off_err);
   if (db->has_rmi) {
     db->rmi[0].leaves_log2 = db->rmi[1].leaves_log2 = o.rmi_leaves_log2;
@@ -176,7 +171,7 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
     cudaFreeAsync(scratch, st);
     if (s != BITS_OK) return fail(s);
   }
-  bits_status s = sample_top_tree(db->bs, db->be, nn, t, db->bucket_log2, db->tree, st);
+  bits_status s = build_levels(db.get(), st);
   if (s != BITS_OK) return fail(s);
   if (db->has_rmi) {
     for (int a = 0; a < 2; ++a) {
@@ -297,6 +292,24 @@ bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_
   if (d_be) *d_be = db->be;
   if (n) *n = db->n;
   if (has_rmi) *has_rmi = db->has_rmi ? 1 : 0;
+  return BITS_OK;
+}
+
+bits_status bits_db_rmi(const bits_db* db, int32_t which, const void** d_leaves,
+                        uint32_t* n_leaves, float* root_slope, float* root_icpt) {
+  if (!db || which < 0 || which > 1) {
+    set_error("bits_db_rmi: bad argument");
+    return BITS_EINVAL;
+  }
+  if (!db->has_rmi) {
+    set_error("bits_db_rmi: database was built without a learned index");
+    return BITS_ENOTIMPL;
+  }
+  const bits_rmi& r = db->rmi[which];
+  if (d_leaves) *d_leaves = r.leaves;
+  if (n_leaves) *n_leaves = 1u << r.leaves_log2;
+  if (root_slope) *root_slope = r.root_slope;
+  if (root_icpt) *root_icpt = r.root_icpt;
   return BITS_OK;
 }
 

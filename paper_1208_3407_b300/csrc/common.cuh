@@ -26,6 +26,7 @@ constexpr uint32_t kU32Max = 0xFFFFFFFFu;
 // Host helpers (defined in capi.cu).
 void set_error(const std::string& msg);
 void count_launch(uint32_t k = 1);
+void uncount_launch(uint64_t k);
 int sm_count();
 bits_status cuda_status(cudaError_t e, const char* what);
 

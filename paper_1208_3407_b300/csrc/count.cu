@@ -1,114 +1,165 @@
-// bits_count kernels: Algorithm 2's counting loop over Algorithm 1 (ICount),
-// one thread per pair of queries (Sec. 2.4 assigns one ICount per thread;
-// two per thread here give four independent searches in flight).
+// bits_count kernels: Algorithm 2's counting loop over Algorithm 1 (ICount).
 //
-// Per thread: one 16-byte load of two (start, end) queries, four searches
-// (two ranks per query) through the shared-memory top tree and then through
-// the 2^k-element bucket in global memory, one 8-byte store of the two
-// counts, and a block reduction of the 64-bit total with one atomic per CTA.
+// One thread per query (Sec. 2.4 assigns one ICount per thread): a coalesced
+// 8-byte load of (start, end), the two top-level searches in shared memory,
+// the quad-cooperative descent through the 16-ary levels (search.cuh), a
+// coalesced 4-byte store of the count, and a block reduction of the 64-bit
+// total with one atomic per CTA.
+//
+// Also here: k_build_levels, which writes the implicit 16-ary tree of both
+// sorted arrays after the sort.
 #include "count.cuh"
 #include "search.cuh"
 
 namespace bits {
 namespace {
 
-constexpr int kCountBlock = 256;
+constexpr int kCountBlock = 512;
 
-template <bool VEC>
-__global__ void __launch_bounds__(kCountBlock)
-k_count_search(const uint2* __restrict__ a, uint32_t n, const uint32_t* __restrict__ bs,
-               const uint32_t* __restrict__ be, uint32_t nb, const uint32_t* __restrict__ tree,
-               int t, int k, uint32_t* __restrict__ counts,
-               unsigned long long* __restrict__ total, uint32_t* __restrict__ err) {
-  extern __shared__ __align__(16) uint32_t s_tree[];
+__global__ void __launch_bounds__(kCountBlock, 2)
+k_count_search(const uint2* __restrict__ a, uint32_t n, LevelIndex L, uint32_t nb,
+               uint32_t* __restrict__ counts, unsigned long long* __restrict__ total,
+               uint32_t* __restrict__ err) {
+  extern __shared__ __align__(16) uint32_t s_top[];
   __shared__ unsigned long long s_red[32];
-  const uint32_t tsz = 1u << t;
-  load_tree(s_tree, tree, tsz);
+  load_top(s_top, L);
   __syncthreads();
 
   unsigned long long acc = 0ull;
   bool bad = false;
-  const uint32_t npairs = (n >> 1) + (n & 1u);
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs;
-       p += gridDim.x * blockDim.x) {
-    const bool has1 = 2u * p + 1u < n;
-    uint32_t s0, e0, s1 = 0u, e1 = 0u;
-    if (VEC && has1) {
-      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(a) + p);
-      s0 = q.x; e0 = q.y; s1 = q.z; e1 = q.w;
-    } else {
-      const uint2 q0 = __ldcs(a + 2u * p);
-      s0 = q0.x; e0 = q0.y;
-      if (has1) {
-        const uint2 q1 = __ldcs(a + 2u * p + 1u);
-        s1 = q1.x; e1 = q1.y;
-      }
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const uint32_t i = base + threadIdx.x;
+    const bool valid = i < n;
+    uint2 q = make_uint2(0u, 0u);
+    if (valid) q = __ldcs(a + i);
+    const uint32_t key_s = q.y, key_e = q.x + 1u;
+    uint32_t rs, re;
+    top_rank2(s_top, L.top_size, key_s, key_e, rs, re);
+    quad_descend(L, rs, key_s, re, key_e);
+    uint32_t c = icount_from_ranks(rs, re, q.x, nb);
+    if (q.y < q.x) {
+      c = 0u;
+      bad = true;
     }
-    const uint32_t key[4] = {e0, s0 + 1u, e1, s1 + 1u};
-    uint32_t pos[4];
-    rank_lt_tree<4>(s_tree, tsz, bs, be, nb, k, key, pos);
-    uint32_t c0 = icount_from_ranks(pos[0], pos[1], s0, nb);
-    uint32_t c1 = icount_from_ranks(pos[2], pos[3], s1, nb);
-    if (e0 < s0) { c0 = 0u; bad = true; }
-    if (e1 < s1) { c1 = 0u; bad = true; }
-    if (!has1) c1 = 0u;
-    if (counts) {
-      if (VEC && has1) {
-        __stcs(reinterpret_cast<uint2*>(counts) + p, make_uint2(c0, c1));
-      } else {
-        counts[2u * p] = c0;
-        if (has1) counts[2u * p + 1u] = c1;
-      }
+    if (valid) {
+      if (counts) __stcs(counts + i, c);
+      acc += c;
     }
-    acc += (unsigned long long)c0 + c1;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_dev_error(err, DEV_ERR_INVALID);
   const unsigned long long sum = block_sum_u64(acc, s_red);
   if (threadIdx.x == 0 && sum) atomicAdd(total, sum);
 }
 
-template <bool VEC>
-int count_grid(size_t smem) {
-  static int per_sm[2] = {0, 0};
-  static size_t smem_for[2] = {0, 0};
-  const int slot = VEC ? 1 : 0;
-  if (per_sm[slot] == 0 || smem_for[slot] != smem) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_count_search<VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_count_search<VEC>, kCountBlock, smem);
-    per_sm[slot] = std::max(1, b);
-    smem_for[slot] = smem;
+struct LevelJob {
+  uint32_t* out;
+  const uint32_t* src;  // sorted array the level samples
+  uint32_t count;       // entries to write (real + padding)
+  uint32_t real;        // real entries; the rest are 0xFFFFFFFF
+  int shift;            // 4 * level
+};
+struct LevelJobs {
+  LevelJob j[2 * (kMaxLevels + 2)];
+};
+
+__global__ void k_build_levels(LevelJobs jobs, uint32_t n) {
+  const LevelJob* J = &jobs.j[blockIdx.y];
+  uint32_t* out = J->out;
+  const uint32_t* src = J->src;
+  const uint32_t count = J->count, real = J->real;
+  const int shift = J->shift;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    uint32_t v = kU32Max;
+    if (i < real) {
+      const uint64_t end = min(((uint64_t)i + 1u) << shift, (uint64_t)n);
+      v = src[end - 1];
+    }
+    out[i] = v;
   }
-  return per_sm[slot];
+}
+
+int count_blocks_per_sm(size_t smem) {
+  static int per_sm = 0;
+  static size_t smem_for = 0;
+  if (per_sm == 0 || smem_for != smem) {
+    cudaFuncSetAttribute(k_count_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_count_search, kCountBlock, smem);
+    per_sm = std::max(1, b);
+    smem_for = smem;
+  }
+  return per_sm;
 }
 
 }  // namespace
+
+uint32_t round16(uint32_t x) { return (x + 15u) & ~15u; }
+
+void plan_levels(uint32_t n, int top_log2, LevelPlan& p) {
+  const uint32_t cap = (1u << top_log2) - 1u;
+  p.len[0] = n;
+  int J = 0;
+  // Past level kMaxLevels-1 the top simply grows (at most 1024 entries for n < 2^30).
+  while (p.len[J] > cap && J < kMaxLevels - 1) {
+    p.len[J + 1] = (uint32_t)(((uint64_t)p.len[J] + 15u) / 16u);
+    ++J;
+  }
+  p.J = J;
+  uint32_t ts = 4;
+  while (ts < p.len[J] + 1u) ts <<= 1;
+  p.top_size = ts;
+  // words of the stored levels 1 .. J-1 (per array), each padded to 16
+  size_t words = 0;
+  for (int j = 1; j < J; ++j) {
+    p.off[j] = words;
+    words += round16(p.len[j]);
+  }
+  p.level_words = words;
+}
+
+bits_status build_levels(bits_db* db, cudaStream_t st) {
+  const LevelPlan& p = db->plan;
+  LevelIndex& L = db->lvl;
+  L.J = p.J;
+  L.top_size = p.top_size;
+  L.top = db->top;
+  for (int j = 0; j <= p.J; ++j) L.len[j] = p.len[j];
+  for (int a = 0; a < 2; ++a) {
+    uint32_t* X = a ? db->be : db->bs;
+    L.lv[a][0] = X;
+    for (int j = 1; j < p.J; ++j) L.lv[a][j] = db->levels + a * p.level_words + p.off[j];
+  }
+  LevelJobs jobs{};
+  int nj = 0;
+  for (int a = 0; a < 2; ++a) {
+    uint32_t* X = a ? db->be : db->bs;
+    // level 0 padding
+    jobs.j[nj++] = LevelJob{X + db->n, X, round16(db->n) - db->n, 0u, 0};
+    for (int j = 1; j < p.J; ++j)
+      jobs.j[nj++] = LevelJob{db->levels + a * p.level_words + p.off[j], X, round16(p.len[j]),
+                              p.len[j], 4 * j};
+    jobs.j[nj++] = LevelJob{db->top + a * p.top_size, X, p.top_size, p.len[p.J], 4 * p.J};
+  }
+  uint32_t biggest = 1;
+  for (int k = 0; k < nj; ++k) biggest = std::max(biggest, jobs.j[k].count);
+  const dim3 grid(std::min<uint32_t>((biggest + 255) / 256, 4096), nj);
+  k_build_levels<<<grid, 256, 0, st>>>(jobs, db->n);
+  BITS_LAUNCH_CHECK("k_build_levels");
+  return BITS_OK;
+}
 
 bits_status launch_count_search(const bits_db* db, const uint32_t* d_a, uint32_t n,
                                 uint32_t* d_counts, uint64_t* d_total, cudaStream_t st) {
   BITS_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), st));
   if (n == 0) return BITS_OK;
-  const uint32_t tsz = 1u << db->tree_log2;
-  const size_t smem = sizeof(uint32_t) * 2 * tsz;
-  const bool vec = (reinterpret_cast<uintptr_t>(d_a) % 16 == 0) &&
-                   (d_counts == nullptr || reinterpret_cast<uintptr_t>(d_counts) % 8 == 0);
-  const uint32_t npairs = (n >> 1) + (n & 1u);
-  const uint32_t need = (npairs + kCountBlock - 1) / kCountBlock;
-  const uint2* a = reinterpret_cast<const uint2*>(d_a);
-  auto* tot = reinterpret_cast<unsigned long long*>(d_total);
-  if (vec) {
-    const uint32_t grid = std::min<uint32_t>(need, (uint32_t)(count_grid<true>(smem) * sm_count()));
-    k_count_search<true><<<grid, kCountBlock, smem, st>>>(a, n, db->bs, db->be, db->n, db->tree,
-                                                          db->tree_log2, db->bucket_log2,
-                                                          d_counts, tot, db->err);
-  } else {
-    const uint32_t grid = std::min<uint32_t>(need, (uint32_t)(count_grid<false>(smem) * sm_count()));
-    k_count_search<false><<<grid, kCountBlock, smem, st>>>(a, n, db->bs, db->be, db->n, db->tree,
-                                                           db->tree_log2, db->bucket_log2,
-                                                           d_counts, tot, db->err);
-  }
+  const size_t smem = sizeof(uint32_t) * 2 * db->lvl.top_size;
+  const uint32_t need = (n + kCountBlock - 1) / kCountBlock;
+  const uint32_t grid = std::min<uint32_t>(need, (uint32_t)(count_blocks_per_sm(smem) * sm_count()));
+  k_count_search<<<grid, kCountBlock, smem, st>>>(reinterpret_cast<const uint2*>(d_a), n, db->lvl,
+                                                  db->n, d_counts,
+                                                  reinterpret_cast<unsigned long long*>(d_total),
+                                                  db->err);
   BITS_LAUNCH_CHECK("k_count_search");
   return BITS_OK;
 }

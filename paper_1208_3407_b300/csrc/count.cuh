@@ -1,4 +1,4 @@
-// Host launchers of the counting kernels.
+// Host side of the search index and the counting kernels (count.cu).
 #pragma once
 
 #include "common.cuh"
@@ -6,8 +6,18 @@
 
 namespace bits {
 
-// Plain BITS count: top tree in shared memory + binary search in the bucket.
-// Zeroes *d_total, then accumulates; d_counts may be NULL.
+uint32_t round16(uint32_t x);
+
+// Level sizes of the implicit 16-ary tree over n sorted keys whose top level
+// holds at most 2^top_log2 - 1 entries.
+void plan_levels(uint32_t n, int top_log2, LevelPlan& p);
+
+// Fill db->lvl and write the level storage, the top images and the level-0
+// padding from the sorted arrays db->bs / db->be.
+bits_status build_levels(bits_db* db, cudaStream_t st);
+
+// Plain BITS count through the 16-ary levels.  Zeroes *d_total, then
+// accumulates; d_counts may be NULL.
 bits_status launch_count_search(const bits_db* db, const uint32_t* d_a, uint32_t n,
                                 uint32_t* d_counts, uint64_t* d_total, cudaStream_t st);
 

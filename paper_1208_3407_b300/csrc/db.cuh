@@ -7,6 +7,7 @@
 #include <tuple>
 
 #include "common.cuh"
+#include "search.cuh"
 
 // One sorted array's learned index (a two-stage recursive model): a linear
 // root maps a key to one of 2^L leaves; each leaf is a linear model of the
@@ -33,14 +34,24 @@ struct bits_rmi {
 
 struct bits_mc_graph;  // cached CUDA graph of one bits_mc argument set (mc.cu)
 
+// Sizes of the implicit 16-ary tree (see search.cuh).
+struct LevelPlan {
+  int J = 0;                           // top level, kept in shared memory
+  uint32_t len[bits::kMaxLevels + 1] = {};
+  size_t off[bits::kMaxLevels] = {};   // word offset of level j (1 <= j < J) in one array's storage
+  size_t level_words = 0;              // words of levels 1 .. J-1 per array
+  uint32_t top_size = 4;               // shared-memory entries per array (power of two)
+};
+
 struct bits_db {
   int device = 0;
   uint32_t n = 0;
-  uint32_t* bs = nullptr;    // sorted starts (device)
-  uint32_t* be = nullptr;    // sorted ends (device)
-  uint32_t* tree = nullptr;  // start tree [2^t] then end tree [2^t] (device)
-  int tree_log2 = 12;        // t
-  int bucket_log2 = 0;       // k: every bucket holds 2^k ranks
+  uint32_t* bs = nullptr;      // sorted starts, padded with 0xFFFFFFFF to 16 (device)
+  uint32_t* be = nullptr;      // sorted ends, padded the same way (device)
+  uint32_t* levels = nullptr;  // levels 1 .. J-1 of both arrays (device)
+  uint32_t* top = nullptr;     // top-level images [2][top_size] (device)
+  LevelPlan plan;
+  bits::LevelIndex lvl{};      // kernel-side view of the levels
   uint32_t* err = nullptr;   // device error word (DEV_ERR_* bits)
   int method = BITS_METHOD_SEARCH;
   bool has_rmi = false;
@@ -54,3 +65,9 @@ struct bits_db {
            std::shared_ptr<bits_mc_graph>>
       mc_graphs;
 };
+
+namespace bits {
+// Synchronise `st`, read the database's device error word (and clear it if
+// asked) and turn it into a status.
+bits_status read_device_error(const bits_db* db, cudaStream_t st, bool clear);
+}  // namespace bits

@@ -1,14 +1,286 @@
+// Monte-Carlo significance test (Sec. 3.2): each shuffle re-places every
+// query interval uniformly inside its own contig (length kept) and recounts
+// it against the fixed database; the observed total is the count of the
+// unshuffled queries; k_ge = #{s : total_s >= observed}.
+//
+// k_mc_search is persistent.  A work unit is (chunk of 1024 intervals,
+// block of 256 shuffles); a thread owns one shuffle, so the block walks the
+// chunk's intervals out of shared memory (a broadcast read) and keeps its
+// shuffle's running total in a register: one atomic per thread per unit, no
+// reduction tree.  Per placement: one Philox4x32-10 block, a multiply-high
+// offset, and the two rank searches of search.cuh (shared-memory top level,
+// then quad-cooperative 64-byte chunks, which for a 1M-interval database all
+// sit in L2).  The interval's contig is found when the chunk is staged.
+//
+// A call runs as a CUDA graph (zero totals, observed count, persistent MC
+// launch, tally) captured once per argument set and replayed afterwards.
+#include <vector>
+
+#include "count.cuh"
 #include "mc.cuh"
+#include "philox.cuh"
+#include "rmi.cuh"
+#include "rmi_search.cuh"
+#include "search.cuh"
+
+struct bits_mc_graph {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  unsigned long long* d_scalars = nullptr;  // [0] observed, [1] k_ge
+  uint64_t kernels_per_replay = 0;
+  ~bits_mc_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (d_scalars) cudaFree(d_scalars);
+  }
+};
 
 namespace bits {
+namespace {
 
-bits_status run_mc(bits_db*, int, const uint32_t*, uint32_t, const uint32_t*, const uint32_t*,
-                   uint32_t, uint64_t, uint32_t, uint32_t, uint64_t*, uint64_t*, uint64_t*,
-                   double*, cudaStream_t) {
-  set_error("bits_mc: not built yet");
-  return BITS_ENOTIMPL;
+constexpr int kMcBlock = 256;    // shuffles per work unit (one per thread)
+constexpr int kMcChunk = 1024;   // intervals per work unit
+constexpr int kMaxContigs = 4096;
+
+struct McArgs {
+  const uint2* a;
+  uint32_t n;
+  const uint32_t* coff;
+  const uint32_t* clen;
+  uint32_t nc;
+  uint32_t key0, key1;
+  uint32_t s_begin, n_shuffles;
+  unsigned long long* totals;
+  uint32_t* err;
+  uint32_t nb;
+};
+
+// Contig of a position: last contig whose offset is <= pos, or -1.
+__device__ __forceinline__ int contig_of(const uint32_t* s_coff, uint32_t nc, uint32_t pos) {
+  uint32_t lo = 0, len = nc;  // count of offsets <= pos
+  while (len > 0) {
+    const uint32_t half = len >> 1;
+    if (s_coff[lo + half] <= pos) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return (int)lo - 1;
 }
 
-void release_mc_graphs(bits_db* db) { db->mc_graphs.clear(); }
+template <bool kRmi>
+__global__ void __launch_bounds__(kMcBlock)
+k_mc_search(McArgs P, LevelIndex L, RmiView R) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* s_top = smem;
+  uint32_t* s_off = s_top + (kRmi ? 0u : 2u * L.top_size);
+  uint32_t* s_rng = s_off + kMcChunk;
+  uint32_t* s_len = s_rng + kMcChunk;
+  uint32_t* s_coff = s_len + kMcChunk;
+  uint32_t* s_clen = s_coff + P.nc;
+
+  if (!kRmi) load_top(s_top, L);
+  for (uint32_t c = threadIdx.x; c < P.nc; c += blockDim.x) {
+    s_coff[c] = P.coff[c];
+    s_clen[c] = P.clen[c];
+  }
+  const uint32_t n_chunks = (P.n + kMcChunk - 1) / kMcChunk;
+  const uint32_t n_sblocks = (P.n_shuffles + kMcBlock - 1) / kMcBlock;
+  const uint32_t units = n_chunks * n_sblocks;
+  bool bad = false;
+  for (uint32_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const uint32_t chunk = u % n_chunks, sb = u / n_chunks;
+    const uint32_t i0 = chunk * kMcChunk;
+    const uint32_t cn = min((uint32_t)kMcChunk, P.n - i0);
+    __syncthreads();  // previous unit is done with the staged chunk
+    for (uint32_t k = threadIdx.x; k < cn; k += blockDim.x) {
+      const uint2 q = P.a[i0 + k];
+      const int c = contig_of(s_coff, P.nc, q.x);
+      const bool ok = c >= 0 && q.y >= q.x &&
+                      (unsigned long long)q.y <= (unsigned long long)s_coff[c] + s_clen[c];
+      if (ok) {
+        s_off[k] = s_coff[c];
+        s_len[k] = q.y - q.x;
+        s_rng[k] = s_clen[c] - (q.y - q.x) + 1u;
+      } else {
+        bad = true;
+        s_off[k] = q.x;
+        s_len[k] = 0u;
+        s_rng[k] = 1u;
+      }
+    }
+    __syncthreads();
+    const uint32_t s_local = sb * kMcBlock + threadIdx.x;
+    const uint32_t s = P.s_begin + s_local;
+    unsigned long long acc = 0ull;
+    for (uint32_t k = 0; k < cn; ++k) {
+      const uint32_t off = s_off[k], rng = s_rng[k], len = s_len[k];
+      const uint4 x = philox4x32_10(make_uint4(i0 + k, s, 0u, 0u), P.key0, P.key1);
+      const uint32_t start = off + philox_offset(x, rng);
+      const uint32_t end = start + len;
+      uint32_t rs, re;
+      const uint32_t key_s = end, key_e = start + 1u;
+      if (kRmi) {
+        rmi_rank2(R, L, P.nb, key_s, key_e, rs, re);
+      } else {
+        top_rank2(s_top, L.top_size, key_s, key_e, rs, re);
+        quad_descend(L, rs, key_s, re, key_e);
+      }
+      acc += icount_from_ranks(rs, re, start, P.nb);
+    }
+    if (s_local < P.n_shuffles && acc) atomicAdd(P.totals + s_local, acc);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) set_dev_error(P.err, DEV_ERR_INVALID);
+}
+
+__global__ void k_mc_tally(const unsigned long long* __restrict__ totals, uint32_t n,
+                           unsigned long long* scalars) {
+  __shared__ unsigned long long s_red[32];
+  const unsigned long long obs = scalars[0];
+  unsigned long long k = 0;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) k += totals[i] >= obs;
+  k = block_sum_u64(k, s_red);
+  if (threadIdx.x == 0) scalars[1] = k;
+}
+
+size_t mc_smem_bytes(const LevelIndex& L, uint32_t nc, bool rmi) {
+  return sizeof(uint32_t) * ((rmi ? 0 : 2 * L.top_size) + 3 * kMcChunk + 2 * nc);
+}
+
+template <bool kRmi>
+int mc_blocks_per_sm(size_t smem) {
+  static int per_sm = 0;
+  static size_t smem_for = 0;
+  if (per_sm == 0 || smem_for != smem) {
+    cudaFuncSetAttribute(k_mc_search<kRmi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mc_search<kRmi>, kMcBlock, smem);
+    per_sm = std::max(1, b);
+    smem_for = smem;
+  }
+  return per_sm;
+}
+
+// Enqueue the whole test on `st` (used once, under stream capture).
+bits_status enqueue_mc(bits_db* db, int method, const uint32_t* d_a, uint32_t n,
+                       const uint32_t* d_contig_off, const uint32_t* d_contig_len,
+                       uint32_t n_contigs, uint64_t seed, uint32_t shuffle_begin,
+                       uint32_t n_shuffles, uint64_t* d_totals, unsigned long long* d_scalars,
+                       cudaStream_t st) {
+  if (n_shuffles)
+    BITS_CUDA_TRY(cudaMemsetAsync(d_totals, 0, sizeof(uint64_t) * n_shuffles, st));
+  // Observed total of the unshuffled queries (Algorithm 2 on A itself).
+  bits_status s = method == BITS_METHOD_RMI
+                      ? launch_count_rmi(db, d_a, n, nullptr, reinterpret_cast<uint64_t*>(d_scalars), st)
+                      : launch_count_search(db, d_a, n, nullptr,
+                                            reinterpret_cast<uint64_t*>(d_scalars), st);
+  if (s != BITS_OK) return s;
+  if (n && n_shuffles) {
+    McArgs P{};
+    P.a = reinterpret_cast<const uint2*>(d_a);
+    P.n = n;
+    P.coff = d_contig_off;
+    P.clen = d_contig_len;
+    P.nc = n_contigs;
+    P.key0 = (uint32_t)seed;
+    P.key1 = (uint32_t)(seed >> 32);
+    P.s_begin = shuffle_begin;
+    P.n_shuffles = n_shuffles;
+    P.totals = reinterpret_cast<unsigned long long*>(d_totals);
+    P.err = db->err;
+    P.nb = db->n;
+    const bool rmi = method == BITS_METHOD_RMI;
+    const size_t smem = mc_smem_bytes(db->lvl, n_contigs, rmi);
+    const uint32_t units = ((n + kMcChunk - 1) / kMcChunk) *
+                           ((n_shuffles + kMcBlock - 1) / kMcBlock);
+    const RmiView R = db->has_rmi ? rmi_view(db) : RmiView{};
+    if (rmi) {
+      const uint32_t grid =
+          std::min<uint32_t>(units, (uint32_t)(mc_blocks_per_sm<true>(smem) * sm_count()));
+      k_mc_search<true><<<grid, kMcBlock, smem, st>>>(P, db->lvl, R);
+    } else {
+      const uint32_t grid =
+          std::min<uint32_t>(units, (uint32_t)(mc_blocks_per_sm<false>(smem) * sm_count()));
+      k_mc_search<false><<<grid, kMcBlock, smem, st>>>(P, db->lvl, R);
+    }
+    BITS_LAUNCH_CHECK("k_mc_search");
+  }
+  k_mc_tally<<<1, 1024, 0, st>>>(reinterpret_cast<const unsigned long long*>(d_totals), n_shuffles,
+                                 d_scalars);
+  BITS_LAUNCH_CHECK("k_mc_tally");
+  return BITS_OK;
+}
+
+}  // namespace
+
+bits_status run_mc(bits_db* db, int method, const uint32_t* d_a, uint32_t n,
+                   const uint32_t* d_contig_off, const uint32_t* d_contig_len, uint32_t n_contigs,
+                   uint64_t seed, uint32_t shuffle_begin, uint32_t shuffle_end, uint64_t* d_totals,
+                   uint64_t* h_observed, uint64_t* h_k_ge, double* h_pvalue, cudaStream_t st) {
+  if (n_contigs > kMaxContigs) {
+    set_error("bits_mc: at most 4096 contigs");
+    return BITS_EOVERFLOW;
+  }
+  if (reinterpret_cast<uintptr_t>(d_a) % 8 || reinterpret_cast<uintptr_t>(d_totals) % 8) {
+    set_error("bits_mc: misaligned pointer (queries 8 B, totals 8 B)");
+    return BITS_EINVAL;
+  }
+  const uint32_t n_shuffles = shuffle_end - shuffle_begin;
+  auto key = std::make_tuple(method, (const void*)d_a, (uint64_t)n, (const void*)d_contig_off,
+                             (const void*)d_contig_len, n_contigs, seed, shuffle_begin,
+                             shuffle_end, (void*)d_totals, (void*)nullptr);
+  std::shared_ptr<bits_mc_graph> g;
+  {
+    std::lock_guard<std::mutex> lk(db->mu);
+    auto it = db->mc_graphs.find(key);
+    if (it != db->mc_graphs.end()) g = it->second;
+  }
+  if (!g) {
+    g = std::make_shared<bits_mc_graph>();
+    BITS_CUDA_TRY(cudaMalloc(&g->d_scalars, 2 * sizeof(unsigned long long)));
+    cudaStream_t cap = nullptr;
+    BITS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    const uint64_t before = bits_kernel_launches();
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return cuda_status(e, "cudaStreamBeginCapture");
+    }
+    bits_status s = enqueue_mc(db, method, d_a, n, d_contig_off, d_contig_len, n_contigs, seed,
+                               shuffle_begin, n_shuffles, d_totals, g->d_scalars, cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (s != BITS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+    g->graph = graph;
+    BITS_CUDA_TRY(cudaGraphInstantiate(&g->exec, graph, 0));
+    g->kernels_per_replay = bits_kernel_launches() - before;
+    uncount_launch(g->kernels_per_replay);
+    std::lock_guard<std::mutex> lk(db->mu);
+    db->mc_graphs[key] = g;
+  }
+  BITS_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+  count_launch((uint32_t)g->kernels_per_replay);
+  unsigned long long h[2] = {0, 0};
+  BITS_CUDA_TRY(cudaMemcpyAsync(h, g->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, st));
+  bits_status s = read_device_error(db, st, true);
+  if (s != BITS_OK) return s;
+  if (h_observed) *h_observed = h[0];
+  if (h_k_ge) *h_k_ge = h[1];
+  if (h_pvalue) *h_pvalue = (double)(h[1] + 1) / (double)((uint64_t)n_shuffles + 1);
+  return BITS_OK;
+}
+
+void release_mc_graphs(bits_db* db) {
+  std::lock_guard<std::mutex> lk(db->mu);
+  db->mc_graphs.clear();
+}
 
 }  // namespace bits

@@ -237,22 +237,6 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
   if (oob) set_dev_error(err, DEV_ERR_TIMEOUT);
 }
 
-__global__ void k_sample_tree(const uint32_t* __restrict__ bs, const uint32_t* __restrict__ be,
-                              uint32_t n, int t, int k, uint32_t* __restrict__ tree) {
-  const uint32_t tsz = 1u << t;
-  const uint32_t buckets = (uint32_t)(((uint64_t)n + (1ull << k) - 1) >> k);
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < 2 * tsz; j += gridDim.x * blockDim.x) {
-    const uint32_t jj = j & (tsz - 1);
-    const uint32_t* src = (j >= tsz) ? be : bs;
-    uint32_t v = kU32Max;
-    if (jj < buckets) {
-      const uint64_t end = min((uint64_t)(jj + 1) << k, (uint64_t)n);
-      v = src[end - 1];
-    }
-    tree[j] = v;
-  }
-}
-
 }  // namespace
 
 size_t radix_status_words(uint32_t n) {
@@ -326,15 +310,6 @@ bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, 
     BITS_LAUNCH_CHECK("k_onesweep");
     (void)job_array;
   }
-  return BITS_OK;
-}
-
-bits_status sample_top_tree(const uint32_t* bs, const uint32_t* be, uint32_t n, int t, int k,
-                            uint32_t* tree, cudaStream_t st) {
-  const uint32_t total = 2u << t;
-  const int grid = (int)std::min<uint32_t>((total + 255) / 256, 1024);
-  k_sample_tree<<<grid, 256, 0, st>>>(bs, be, n, t, k, tree);
-  BITS_LAUNCH_CHECK("k_sample_tree");
   return BITS_OK;
 }
 

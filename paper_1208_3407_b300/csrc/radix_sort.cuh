@@ -1,4 +1,4 @@
-// Host interface of the radix sort and top-tree sampler (radix_sort.cu).
+// Host interface of the radix sort (radix_sort.cu).
 #pragma once
 
 #include "common.cuh"
@@ -22,10 +22,5 @@ size_t radix_status_words(uint32_t n);
 // into d_err, returned as BITS_EINVAL); synchronises `st` once.
 bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, uint32_t* out_e,
                                  uint32_t* d_err, RadixScratch& ws, cudaStream_t st);
-
-// tree[0 .. 2^t) = last key of every 2^k-bucket of bs (then padding with
-// 0xFFFFFFFF); tree[2^t .. 2^(t+1)) the same for be.
-bits_status sample_top_tree(const uint32_t* bs, const uint32_t* be, uint32_t n, int t, int k,
-                            uint32_t* tree, cudaStream_t st);
 
 }  // namespace bits

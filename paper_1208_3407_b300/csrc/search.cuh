@@ -1,60 +1,180 @@
 // Device search primitives shared by the counting, Monte-Carlo and all-pairs
-// kernels.  Every primitive returns the exact rank #(B < key) of a key in a
-// sorted uint32 array B -- the BSearch of Algorithm 1 expressed as a count:
+// kernels.  Every primitive returns the exact rank #(X < key) of a key in a
+// sorted uint32 array X -- Algorithm 1's BSearch expressed as a count:
 //     first = #(B_S < a.end)
 //     last  = #(B_E <= a.start) = #(B_E < a.start + 1)   (a.start < 2^32 - 1)
 // so ICount(a) = first - last (Sec. 2.2).  Only one primitive, "count of
 // elements below key", is needed.
+//
+// Implicit 16-ary search tree over each sorted array (built by
+// k_build_levels):
+//     level 0      = X itself, padded with 0xFFFFFFFF to a multiple of 16
+//     level j >= 1 : L_j[i] = X[min((i+1) * 16^j, n) - 1], the last key of
+//                    the i-th block of 16^j keys; also padded to 16 entries.
+// L_j[i] is the last real entry of the 64-byte chunk L_{j-1}[16i, 16i+16),
+// so if i = #(L_j < key) then #(L_{j-1} < key) = 16 i + #(chunk < key).
+// The top level J (at most 8191 entries) lives in shared memory and is
+// searched per thread; every lower level costs one 64-byte chunk, loaded by
+// the four lanes of a quad (16 bytes each, fully coalesced) and counted with
+// two shuffles.  Only the level-0 chunk normally comes from DRAM; the
+// levels above it are 1/16, 1/256, ... of the array and stay in L2.
 #pragma once
 
 #include "common.cuh"
 
 namespace bits {
 
-// Top tree: tree[j] (j < 2^t) is the last key of bucket j = B[j*2^k ..
-// (j+1)*2^k) of the sorted array, padded with 0xFFFFFFFF past the last
-// bucket.  Searching the 2^t - 1 real slots finds the bucket that holds the
-// rank; a power-of-two search inside the bucket finishes it.
-//
-// N independent searches advance in lock step so that their loads overlap.
-// Search i looks up key[i] in the start array when i is even and in the end
-// array when i is odd; s_tree holds the start tree then the end tree.
-template <int N>
-__device__ __forceinline__ void rank_lt_tree(const uint32_t* __restrict__ s_tree, uint32_t tsz,
-                                             const uint32_t* __restrict__ bs,
-                                             const uint32_t* __restrict__ be, uint32_t nb, int k,
-                                             const uint32_t (&key)[N], uint32_t (&pos)[N]) {
-  #pragma unroll
-  for (int i = 0; i < N; ++i) pos[i] = 0u;
-  for (uint32_t step = tsz >> 1; step; step >>= 1) {
-    #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const uint32_t* S = s_tree + ((i & 1) ? tsz : 0u);
-      if (S[pos[i] + step - 1u] < key[i]) pos[i] += step;
-    }
-  }
-  #pragma unroll
-  for (int i = 0; i < N; ++i) pos[i] = min(pos[i] << k, nb);
-  for (uint32_t step = (1u << k) >> 1; step; step >>= 1) {
-    #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const uint32_t* B = (i & 1) ? be : bs;
-      const uint32_t idx = pos[i] + step - 1u;
-      const uint32_t v = idx < nb ? __ldg(B + idx) : kU32Max;
-      if (v < key[i]) pos[i] += step;
-    }
-  }
+constexpr int kMaxLevels = 6;  // J <= 5 for n < 2^30 with a 8191-entry top
+
+struct LevelIndex {
+  const uint32_t* lv[2][kMaxLevels];  // [array][j]: storage of level j (j < J); [a][0] = X
+  uint32_t len[kMaxLevels + 1];       // real entries of level j, j <= J
+  const uint32_t* top;                // top level image: [2][top_size], padded with 0xFFFFFFFF
+  uint32_t top_size;                  // power of two >= len[J] + 1, >= 4
+  int J;
+};
+
+__device__ __forceinline__ uint4 ldg4(const uint32_t* p) {
+  return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
-// Cooperative copy of the two top trees (2 << t words) into shared memory.
-__device__ __forceinline__ void load_tree(uint32_t* s_tree, const uint32_t* __restrict__ tree,
-                                          uint32_t tsz) {
-  const uint4* src = reinterpret_cast<const uint4*>(tree);
-  uint4* dst = reinterpret_cast<uint4*>(s_tree);
-  for (uint32_t i = threadIdx.x; i < (2u * tsz) / 4u; i += blockDim.x) dst[i] = src[i];
+__device__ __forceinline__ uint32_t cnt4(const uint4 v, uint32_t key) {
+  return (uint32_t)(v.x < key) + (uint32_t)(v.y < key) + (uint32_t)(v.z < key) +
+         (uint32_t)(v.w < key);
 }
 
-// ICount from the two ranks of a query (start s, end e).
+// #(s[0 .. size-1) < key) for a power-of-two size whose tail is padded with
+// 0xFFFFFFFF; two independent searches in lock step.
+__device__ __forceinline__ void top_rank2(const uint32_t* __restrict__ s_top, uint32_t size,
+                                          uint32_t key_s, uint32_t key_e, uint32_t& is,
+                                          uint32_t& ie) {
+  const uint32_t* s_e = s_top + size;
+  uint32_t ps = 0u, pe = 0u;
+  for (uint32_t step = size >> 1; step; step >>= 1) {
+    if (s_top[ps + step - 1u] < key_s) ps += step;
+    if (s_e[pe + step - 1u] < key_e) pe += step;
+  }
+  is = ps;
+  ie = pe;
+}
+
+// Cooperative copy of the two top-level images into shared memory.
+__device__ __forceinline__ void load_top(uint32_t* s_top, const LevelIndex& L) {
+  const uint4* src = reinterpret_cast<const uint4*>(L.top);
+  uint4* dst = reinterpret_cast<uint4*>(s_top);
+  for (uint32_t i = threadIdx.x; i < (2u * L.top_size) / 4u; i += blockDim.x) dst[i] = src[i];
+}
+
+// Descend the 16-ary levels for the two searches (starts, ends) of every
+// thread.  A search enters at level js (resp. je) with its node index is (ie)
+// there -- its rank within level js -- and leaves with its rank in X (level
+// 0).  Plain search enters every search at the top level J; the learned
+// index enters at the lowest node that holds its predicted window.  jmax is
+// the warp-wide maximum entry level.  All 32 lanes must call it (inactive
+// lanes pass js = je = 0).
+__device__ __forceinline__ void quad_descend_from(const LevelIndex& L, int jmax, int js,
+                                                  uint32_t& is_out, uint32_t key_s, int je,
+                                                  uint32_t& ie_out, uint32_t key_e) {
+  const unsigned lane = lane_id(), sub = lane & 3u, qbase = lane & ~3u;
+  uint32_t is[4], ks[4], ie[4], ke[4];
+  int jss[4], jes[4];
+  #pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    is[o] = __shfl_sync(0xFFFFFFFFu, is_out, qbase | o);
+    ks[o] = __shfl_sync(0xFFFFFFFFu, key_s, qbase | o);
+    ie[o] = __shfl_sync(0xFFFFFFFFu, ie_out, qbase | o);
+    ke[o] = __shfl_sync(0xFFFFFFFFu, key_e, qbase | o);
+    jss[o] = __shfl_sync(0xFFFFFFFFu, js, qbase | o);
+    jes[o] = __shfl_sync(0xFFFFFFFFu, je, qbase | o);
+  }
+  #pragma unroll
+  for (int j = kMaxLevels - 1; j >= 1; --j) {
+    if (j > jmax) continue;
+    const uint32_t lenj = L.len[j], lenm = L.len[j - 1];
+    const uint32_t* LS = L.lv[0][j - 1];
+    const uint32_t* LE = L.lv[1][j - 1];
+    uint4 vs[4], ve[4];
+    #pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      vs[o] = (j <= jss[o] && is[o] < lenj) ? ldg4(LS + 16u * is[o] + 4u * sub)
+                                            : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
+      ve[o] = (j <= jes[o] && ie[o] < lenj) ? ldg4(LE + 16u * ie[o] + 4u * sub)
+                                            : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
+    }
+    #pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      uint32_t cs = cnt4(vs[o], ks[o]), ce = cnt4(ve[o], ke[o]);
+      cs += __shfl_xor_sync(0xFFFFFFFFu, cs, 1);
+      ce += __shfl_xor_sync(0xFFFFFFFFu, ce, 1);
+      cs += __shfl_xor_sync(0xFFFFFFFFu, cs, 2);
+      ce += __shfl_xor_sync(0xFFFFFFFFu, ce, 2);
+      if (j <= jss[o]) is[o] = is[o] < lenj ? 16u * is[o] + cs : lenm;
+      if (j <= jes[o]) ie[o] = ie[o] < lenj ? 16u * ie[o] + ce : lenm;
+    }
+  }
+  is_out = sub == 0 ? is[0] : sub == 1 ? is[1] : sub == 2 ? is[2] : is[3];
+  ie_out = sub == 0 ? ie[0] : sub == 1 ? ie[1] : sub == 2 ? ie[2] : ie[3];
+}
+
+// Plain descent: both searches of every thread enter at the top level J.
+__device__ __forceinline__ void quad_descend(const LevelIndex& L, uint32_t& is_out,
+                                             uint32_t key_s, uint32_t& ie_out, uint32_t key_e) {
+  const unsigned lane = lane_id(), sub = lane & 3u, qbase = lane & ~3u;
+  uint32_t is[4], ks[4], ie[4], ke[4];
+  #pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    is[o] = __shfl_sync(0xFFFFFFFFu, is_out, qbase | o);
+    ks[o] = __shfl_sync(0xFFFFFFFFu, key_s, qbase | o);
+    ie[o] = __shfl_sync(0xFFFFFFFFu, ie_out, qbase | o);
+    ke[o] = __shfl_sync(0xFFFFFFFFu, key_e, qbase | o);
+  }
+  #pragma unroll
+  for (int j = kMaxLevels - 1; j >= 1; --j) {
+    if (j > L.J) continue;
+    const uint32_t lenj = L.len[j], lenm = L.len[j - 1];
+    const uint32_t* LS = L.lv[0][j - 1];
+    const uint32_t* LE = L.lv[1][j - 1];
+    uint4 vs[4], ve[4];
+    #pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      vs[o] = is[o] < lenj ? ldg4(LS + 16u * is[o] + 4u * sub)
+                           : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
+      ve[o] = ie[o] < lenj ? ldg4(LE + 16u * ie[o] + 4u * sub)
+                           : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
+    }
+    #pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      uint32_t cs = cnt4(vs[o], ks[o]), ce = cnt4(ve[o], ke[o]);
+      cs += __shfl_xor_sync(0xFFFFFFFFu, cs, 1);
+      ce += __shfl_xor_sync(0xFFFFFFFFu, ce, 1);
+      cs += __shfl_xor_sync(0xFFFFFFFFu, cs, 2);
+      ce += __shfl_xor_sync(0xFFFFFFFFu, ce, 2);
+      is[o] = is[o] < lenj ? 16u * is[o] + cs : lenm;
+      ie[o] = ie[o] < lenj ? 16u * ie[o] + ce : lenm;
+    }
+  }
+  is_out = sub == 0 ? is[0] : sub == 1 ? is[1] : sub == 2 ? is[2] : is[3];
+  ie_out = sub == 0 ? ie[0] : sub == 1 ? ie[1] : sub == 2 ? ie[2] : ie[3];
+}
+
+// #(X[0 .. n) < key) by a per-thread binary search straight in global
+// memory: the slow exact path the learned index falls back to.
+__device__ __forceinline__ uint32_t rank_lt_global(const uint32_t* __restrict__ X, uint32_t n,
+                                                   uint32_t key) {
+  uint32_t lo = 0, len = n;
+  while (len > 0) {
+    const uint32_t half = len >> 1;
+    if (__ldg(X + lo + half) < key) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return lo;
+}
+
+// ICount of query [s, e) from its two ranks.
 __device__ __forceinline__ uint32_t icount_from_ranks(uint32_t first, uint32_t last_plus,
                                                       uint32_t s, uint32_t nb) {
   const uint32_t last = (s == kU32Max) ? nb : last_plus;
