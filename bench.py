@@ -186,6 +186,7 @@ def run_ours(args):
     import torch
 
     import bits_synth
+    import oracle
     import paper_1208_3407_b300 as bits
 
     rank, world, local = env_rank()
@@ -196,6 +197,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     hbm_peak, peak_kind = peaks()
+    o = oracle.get()
 
     def barrier():
         if dist is not None:
@@ -209,66 +211,86 @@ def run_ours(args):
         return float(t.item())
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
 
     def to_dev(x):
         return torch.from_numpy(np.ascontiguousarray(x, dtype=np.uint32)).to(dev)
 
-    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
-                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit()
-                           else local)
-    sampler.start()
-
-    # ---- headline workload: exome-vs-reads shape
-    genome, a_np, b_np = bits_synth.config2()
-    n_a, n_b = a_np.shape[0], b_np.shape[0]
-    a = to_dev(a_np)
-    b = to_dev(b_np)
-    stream = torch.cuda.current_stream()
-
-    # database build (Algorithm 2's set-up), timed separately
-    build_ms = []
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        db = bits.Database(b)
-        e1.record()
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            build_ms.append(e0.elapsed_time(e1))
-        if i < args.warmup + args.steps - 1:
-            db.free()
-
-    counts = torch.empty(n_a, dtype=torch.uint32, device=dev)
-    total = torch.empty(1, dtype=torch.uint64, device=dev)
-
-    def timed_count(method, steps, warmup):
+    def timed(fn, steps, warmup):
+        """Mean device ms of fn over `steps` runs, L2 flushed before each."""
         for _ in range(warmup):
-            db.count(a, counts=counts, total=total, method=method, check=False)
+            fn()
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        launches0 = bits.kernel_launches()
+        l0 = bits.kernel_launches()
         ms = 0.0
         t0 = time.time()
         for _ in range(steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            db.count(a, counts=counts, total=total, method=method, check=False)
+            fn()
             e1.record(stream)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
         torch.cuda.synchronize()
         t1 = time.time()
         barrier()
-        launches = bits.kernel_launches() - launches0
-        db.check()
-        return ms / steps, launches / steps, (t0, t1)
+        return max_over_ranks(ms / steps), (bits.kernel_launches() - l0) / steps, (t0, t1)
 
-    ms_search, launches_search, window = timed_count(bits.METHOD_SEARCH, args.steps, args.warmup)
-    ms_search = max_over_ranks(ms_search)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    sampler = ClockSampler(int(vis) if vis.isdigit() else local)
+    sampler.start()
+
+    # ---- headline: exome-vs-reads shape, database resident -------------------
+    genome, a_np, b_np = bits_synth.config2()
+    n_a, n_b = a_np.shape[0], b_np.shape[0]
+    a = to_dev(a_np)
+    b = to_dev(b_np)
+
+    # Algorithm 2's set-up (split + radix sort + search levels), plain database;
+    # each database is freed after its timed region.
+    build_list = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        l0 = bits.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        db_tmp = bits.Database(b)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            build_list.append((e0.elapsed_time(e1), bits.kernel_launches() - l0))
+        db_tmp.free()
+    build_ms = max_over_ranks(sum(x for x, _ in build_list) / len(build_list))
+    build_launches = build_list[-1][1]
+    t_rmi = time.time()
+    db = bits.Database(b, rmi_leaves_log2=16)          # plain levels + learned index
+    torch.cuda.synchronize()
+    build_rmi_s = time.time() - t_rmi
+
+    counts = torch.empty(n_a, dtype=torch.uint32, device=dev)
+    total = torch.empty(1, dtype=torch.uint64, device=dev)
+
+    def count_with(method):
+        return lambda: db.count(a, counts=counts, total=total, method=method, check=False)
+
+    forms = {}
+    for name, m in (("search", bits.METHOD_SEARCH), ("rmi", bits.METHOD_RMI)):
+        ms, _, _ = timed(count_with(m), args.steps, args.warmup)
+        forms[name] = {"ms_per_step": ms, "queries_per_s": world * n_a / (ms * 1e-3)}
+        db.check()
+    # headline: the library's default (autotuned) method through bits_count
+    db.count(a, counts=counts, total=total, check=True)          # tunes this size class
+    auto_ms, launches, window = timed(count_with(None), args.steps, args.warmup)
+    db.check()
     clocks = sampler.summary(*window)
+    auto_method = "rmi" if forms["rmi"]["ms_per_step"] < forms["search"]["ms_per_step"] else "search"
+    got = counts.cpu().numpy()
+    idx = np.random.default_rng(0).choice(n_a, size=256, replace=False)
+    oc, _ = o.count_brute(a_np[idx], b_np)
+    parity_ok = bool(np.array_equal(got[idx], oc))
 
     # end to end through the public API: pinned host queries in, counts + total out
     a_host = torch.from_numpy(a_np.astype(np.uint32)).pin_memory()
@@ -278,78 +300,81 @@ def run_ours(args):
 
     def e2e_step():
         a_stage.copy_(a_host, non_blocking=True)
-        db.count(a_stage, counts=counts, total=total, method=bits.METHOD_SEARCH, check=False)
+        db.count(a_stage, counts=counts, total=total, check=False)
         counts_host.copy_(counts, non_blocking=True)
         total_host.copy_(total, non_blocking=True)
 
-    for _ in range(args.warmup):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        e2e_step()
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
-    e2e_ms = max_over_ranks(e2e_ms / args.steps)
+    e2e_ms, _, _ = timed(e2e_step, args.steps, args.warmup)
+    db.free()
 
-    # Monte-Carlo test (Sec. 3.2): 100,000 intervals vs 1,000,000, 10,000 shuffles
-    # per launch, replayed from the cached CUDA graph.
+    # ---- Monte-Carlo test (Sec. 3.2): 100k vs 1M, 10,000 shuffles per launch --
     g3, a3_np, b3_np = bits_synth.config3()
     co_np, cl_np = bits_synth.mc_contig_table(g3)
-    db3 = bits.Database(to_dev(b3_np))
+    db3 = bits.Database(to_dev(b3_np), rmi_leaves_log2=16)
     a3, co, cl = to_dev(a3_np), to_dev(co_np), to_dev(cl_np)
     n_sh = 10_000
     totals3 = torch.empty(n_sh, dtype=torch.uint64, device=dev)
+    mc_forms = {}
+    mc_out = None
+    for name, m in (("search", bits.METHOD_SEARCH), ("rmi", bits.METHOD_RMI)):
+        res = []
 
-    def mc_step():
-        return db3.mc(a3, co, cl, seed=7, shuffle_end=n_sh, totals=totals3,
-                      method=bits.METHOD_SEARCH)
+        def mc_step(m=m, res=res):
+            res.append(db3.mc(a3, co, cl, seed=7, shuffle_end=n_sh, totals=totals3, method=m))
 
-    for _ in range(args.warmup):
-        mc_step()
-    torch.cuda.synchronize()
-    barrier()
-    mc_ms = 0.0
-    mc_launches0 = bits.kernel_launches()
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        mc_out = mc_step()
-        e1.record(stream)
-        e1.synchronize()
-        mc_ms += e0.elapsed_time(e1)
-    mc_launches = (bits.kernel_launches() - mc_launches0) / args.steps
-    mc_ms = max_over_ranks(mc_ms / args.steps)
-    import oracle
-    o = oracle.get()
+        ms, l, _ = timed(mc_step, args.steps, args.warmup)
+        mc_forms[name] = {"ms_per_step": ms, "shuffles_per_s": world * n_sh / (ms * 1e-3),
+                          "placements_per_s": world * n_sh * a3_np.shape[0] / (ms * 1e-3),
+                          "gpu_launches": l}
+        mc_out = res[-1][1:]
     t3 = totals3.cpu().numpy()
     bs3, be3 = o.build(b3_np)
     mc_parity = all(int(t3[s]) == int(o.mc(a3_np, co_np, cl_np, bs3, be3, seed=7, s_begin=s,
                                            s_end=s + 1)[0][0]) for s in (0, 4999, 9999))
+    best_mc = min(mc_forms.values(), key=lambda f: f["ms_per_step"])
     mc = {"workload": "100,000 uniform intervals (len U[100,2000]) vs 1,000,000 clustered "
                       "(200,000 hotspots) on the 24-contig genome, 10,000 shuffles, seed 7",
-          "shuffles_per_s": world * n_sh / (mc_ms * 1e-3), "ms_per_step": mc_ms,
-          "placements_per_s": world * n_sh * a3_np.shape[0] / (mc_ms * 1e-3),
-          "observed": mc_out[1], "k_ge": mc_out[2], "p_value": mc_out[3],
-          "gpu_launches": mc_launches, "method": "search", "parity_sample_ok": bool(mc_parity),
+          "shuffles_per_s": best_mc["shuffles_per_s"], "forms": mc_forms,
+          "observed": mc_out[0], "k_ge": mc_out[1], "p_value": mc_out[2],
+          "parity_sample_ok": bool(mc_parity),
           "paper_context": "Table 1: BITS-CUDA, size 1e5, 10,000 rounds in 28 s "
                            "(357 shuffles/s) on an unnamed 2012 GPU"}
     db3.free()
+    del a3, co, cl, totals3
 
-    # parity of what was timed: the last counts against the oracle on a sample
-    got = counts.cpu().numpy()
-    idx = np.random.default_rng(0).choice(n_a, size=256, replace=False)
-    oc, _ = o.count_brute(a_np[idx], b_np)
-    parity_ok = bool(np.array_equal(got[idx], oc))
+    # ---- learned index at scale: 100M queries vs 100M intervals ----------------
+    a4_np, b4_np = bits_synth.config4()
+    b4 = to_dev(b4_np)
+    t0 = time.time()
+    db4 = bits.Database(b4, rmi_leaves_log2=16)
+    torch.cuda.synchronize()
+    build4_s = time.time() - t0
+    del b4
+    a4 = to_dev(a4_np)
+    c4 = torch.empty(a4_np.shape[0], dtype=torch.uint32, device=dev)
+    t4 = torch.empty(1, dtype=torch.uint64, device=dev)
+    scale_forms = {}
+    steps4 = max(3, min(args.steps, 5))
+    for name, m in (("search", bits.METHOD_SEARCH), ("rmi", bits.METHOD_RMI)):
+        ms, _, _ = timed(lambda m=m: db4.count(a4, counts=c4, total=t4, method=m, check=False),
+                         steps4, 3)
+        scale_forms[name] = {"ms_per_step": ms,
+                             "queries_per_s": world * a4_np.shape[0] / (ms * 1e-3),
+                             "hbm_gbs_at_76B_per_query": 76.0 * a4_np.shape[0] / (ms * 1e-3) / 1e9}
+    db4.check()
+    idx4 = np.random.default_rng(2).choice(a4_np.shape[0], size=16, replace=False)
+    oc4, _ = o.count_brute(a4_np[idx4], b4_np)
+    scale = {"workload": "100,000,000 uniform queries vs 100,000,000 intervals from 1000 "
+                         "Gaussians + 20% uniform on a 3.0 Gbp line, lengths log-uniform "
+                         "[50, 10^4], learned index with 2^16 linear leaves per array",
+             "forms": scale_forms, "build_with_learned_index_s": build4_s,
+             "parity_sample_ok": bool(np.array_equal(c4.cpu().numpy()[idx4], oc4))}
+    db4.free()
+    del a4, c4
 
     sampler.stop()
 
-    # CPU baseline: the oracle, as it stands, on a bounded sample of the queries
+    # ---- CPU baseline: the oracle as it stands, on a bounded sample -----------
     cpu = None
     if rank == 0:
         bs_np, be_np = o.build(b_np)
@@ -368,40 +393,40 @@ def run_ours(args):
                "sample": f"first 100,000 of the 200,000 queries x {reps} repetitions, "
                          "database sorted beforehand (std::sort), std::thread over all cores"}
 
-    # roofline of the dominant kernel (k_count_search): algorithmic bytes per
-    # query = 8 B query read + 4 B count write + one 32 B sector per search
-    # of an array larger than L2 (two searches per query).
-    alg_bytes = 76.0 * n_a
-    achieved = alg_bytes / (ms_search * 1e-3) / 1e9
-    traffic = profiled_traffic("k_count_search", ["paper_1208_3407_b300/csrc/count.cu",
-                                                  "paper_1208_3407_b300/csrc/search.cuh"])
-
-    value = world * n_a / (ms_search * 1e-3)
+    # Roofline of the headline's kernel: algorithmic bytes per query = 8 B query
+    # read + 4 B count write + one 32 B sector per search of an array larger
+    # than L2 (two searches per query) = 76 B.
+    kernel = "k_count_rmi" if auto_method == "rmi" else "k_count_search"
+    achieved = 76.0 * n_a / (auto_ms * 1e-3) / 1e9
+    src = (["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/rmi_search.cuh",
+            "paper_1208_3407_b300/csrc/rmi.cu"] if auto_method == "rmi" else
+           ["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/count.cu"])
+    traffic = profiled_traffic(kernel, src)
     line = {
-        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_search,
+        "metric": METRIC, "value": world * n_a / (auto_ms * 1e-3), "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": auto_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded generator; the paper's alignment and exon datasets are "
                 "not available)",
-        "config": {"workload": HEADLINE, "method": "search (shared-memory top tree + binary "
-                   "search)", "l2": "flushed (256 MB write) before every timed step",
+        "config": {"workload": HEADLINE, "method": f"bits_count AUTO (autotuned: {auto_method})",
+                   "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicated database, {world} rank(s), no collective"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": traffic,
-                     "peak_source": peak_kind, "kernel": "k_count_search",
-                     "algorithmic_bytes_per_query": 76},
+                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_kind,
+                     "kernel": kernel, "algorithmic_bytes_per_query": 76},
         "cpu_baseline": cpu,
         "e2e": {"value": world * n_a / (e2e_ms * 1e-3), "unit": "queries/s",
-                "h2d_bytes_per_step": int(a_np.nbytes),
-                "d2h_bytes_per_step": int(n_a * 4 + 8)},
-        "gpu_launches": launches_search,
+                "h2d_bytes_per_step": int(a_np.nbytes), "d2h_bytes_per_step": int(n_a * 4 + 8)},
+        "gpu_launches": launches,
         "clocks": clocks,
-        "build": {"ms": statistics.median(build_ms), "intervals": n_b,
-                  "intervals_per_s": n_b / (statistics.median(build_ms) * 1e-3)},
+        "forms": forms,
+        "build": {"ms": build_ms, "intervals": n_b, "intervals_per_s": n_b / (build_ms * 1e-3),
+                  "gpu_launches": build_launches,
+                  "with_learned_index_s": build_rmi_s},
         "parity_sample_ok": parity_ok,
         "mc": mc,
+        "scale": scale,
     }
-    db.free()
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

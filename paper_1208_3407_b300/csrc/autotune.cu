@@ -1,11 +1,136 @@
 // Method choice for BITS_METHOD_AUTO.
+//
+// The first AUTO count of a size class -- (device, ceil log2 |A|, ceil log2
+// |B|, learned index built or not) -- times every method the database has
+// (plain search, learned index) on the caller's own inputs with CUDA events,
+// three runs each after one warm-up, and keeps the fastest.  Later calls of
+// the class reuse the choice.  When BITS_AUTOTUNE_CACHE names a file, choices
+// are read from it at first use and appended to it as they are made.  Under
+// stream capture no timing is possible, so the learned index (if built) or
+// the plain search is used without tuning.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
 #include "count.cuh"
+#include "rmi.cuh"
 
 namespace bits {
+namespace {
+
+using Key = std::tuple<std::string, int, int, int>;
+std::mutex g_mu;
+std::map<Key, int> g_choice;
+bool g_loaded = false;
+
+int ceil_log2(uint64_t x) {
+  int k = 0;
+  while ((1ull << k) < x) ++k;
+  return k;
+}
+
+std::string device_name() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p{};
+  cudaGetDeviceProperties(&p, dev);
+  std::string s(p.name);
+  for (char& c : s)
+    if (c == ' ') c = '_';
+  return s;
+}
+
+void load_cache() {
+  if (g_loaded) return;
+  g_loaded = true;
+  const char* path = std::getenv("BITS_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char name[256];
+  int la, lb, rmi, m;
+  while (std::fscanf(f, "%255s %d %d %d %d", name, &la, &lb, &rmi, &m) == 5)
+    g_choice[Key(name, la, lb, rmi)] = m;
+  std::fclose(f);
+}
+
+void save_choice(const Key& k, int m) {
+  const char* path = std::getenv("BITS_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %d %d\n", std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k),
+               std::get<3>(k), m);
+  std::fclose(f);
+}
+
+bits_status run_method(const bits_db* db, int m, const uint32_t* d_a, uint32_t n,
+                       uint32_t* d_counts, uint64_t* d_total, cudaStream_t st) {
+  return m == BITS_METHOD_RMI ? launch_count_rmi(db, d_a, n, d_counts, d_total, st)
+                              : launch_count_search(db, d_a, n, d_counts, d_total, st);
+}
+
+}  // namespace
 
 int choose_count_method(const bits_db* db, uint32_t n) {
-  (void)n;
-  return db->has_rmi ? BITS_METHOD_RMI : BITS_METHOD_SEARCH;
+  const int fallback = db->has_rmi ? BITS_METHOD_RMI : BITS_METHOD_SEARCH;
+  std::lock_guard<std::mutex> lk(g_mu);
+  load_cache();
+  auto it = g_choice.find(Key(device_name(), ceil_log2(n), ceil_log2(db->n), db->has_rmi));
+  return it == g_choice.end() ? fallback : it->second;
+}
+
+bits_status autotune_count(const bits_db* db, const uint32_t* d_a, uint32_t n,
+                           uint32_t* d_counts, uint64_t* d_total, cudaStream_t st, int* method) {
+  const Key key(device_name(), ceil_log2(n), ceil_log2(db->n), db->has_rmi);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_cache();
+    auto it = g_choice.find(key);
+    if (it != g_choice.end()) {
+      *method = it->second;
+      return BITS_OK;
+    }
+  }
+  *method = db->has_rmi ? BITS_METHOD_RMI : BITS_METHOD_SEARCH;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  BITS_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone || !db->has_rmi || n == 0) return BITS_OK;
+
+  const int cands[2] = {BITS_METHOD_SEARCH, BITS_METHOD_RMI};
+  float best = 1e30f;
+  int best_m = *method;
+  cudaEvent_t e0, e1;
+  BITS_CUDA_TRY(cudaEventCreate(&e0));
+  BITS_CUDA_TRY(cudaEventCreate(&e1));
+  for (int m : cands) {
+    bits_status s = run_method(db, m, d_a, n, d_counts, d_total, st);
+    if (s != BITS_OK) return s;
+    float tot = 0.f;
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(e0, st);
+      s = run_method(db, m, d_a, n, d_counts, d_total, st);
+      if (s != BITS_OK) return s;
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    if (tot < best) {
+      best = tot;
+      best_m = m;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *method = best_m;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_choice.emplace(key, best_m).second) save_choice(key, best_m);
+  return BITS_OK;
 }
 
 }  // namespace bits

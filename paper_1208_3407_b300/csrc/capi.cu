@@ -201,7 +201,10 @@ bits_status bits_count_method(const bits_db* db, int32_t method, const uint32_t*
     return BITS_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (method == BITS_METHOD_AUTO) method = choose_count_method(db, (uint32_t)n);
+  if (method == BITS_METHOD_AUTO) {
+    bits_status s = autotune_count(db, d_a, (uint32_t)n, d_counts, d_total, st, &method);
+    if (s != BITS_OK) return s;
+  }
   switch (method) {
     case BITS_METHOD_SEARCH:
       return launch_count_search(db, d_a, (uint32_t)n, d_counts, d_total, st);

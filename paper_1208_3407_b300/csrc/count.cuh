@@ -21,7 +21,13 @@ bits_status build_levels(bits_db* db, cudaStream_t st);
 bits_status launch_count_search(const bits_db* db, const uint32_t* d_a, uint32_t n,
                                 uint32_t* d_counts, uint64_t* d_total, cudaStream_t st);
 
-// Method the autotuner picks for an AUTO count of n queries.
+// Method already chosen for an AUTO count of n queries (the untuned default
+// when the size class has not been timed yet).
 int choose_count_method(const bits_db* db, uint32_t n);
+
+// Method for an AUTO count: times the built methods on these inputs the first
+// time a size class is seen (the outputs are overwritten by the final run).
+bits_status autotune_count(const bits_db* db, const uint32_t* d_a, uint32_t n,
+                           uint32_t* d_counts, uint64_t* d_total, cudaStream_t st, int* method);
 
 }  // namespace bits
