@@ -281,12 +281,17 @@ def run_ours(args):
         ms, _, _ = timed(count_with(m), args.steps, args.warmup)
         forms[name] = {"ms_per_step": ms, "queries_per_s": world * n_a / (ms * 1e-3)}
         db.check()
-    # headline: the library's default (autotuned) method through bits_count
+    # AUTO (bits_count's default): its autotuner times back to back (warm L2)
     db.count(a, counts=counts, total=total, check=True)          # tunes this size class
-    auto_ms, launches, window = timed(count_with(None), args.steps, args.warmup)
+    auto_ms, _, _ = timed(count_with(None), args.steps, args.warmup)
+    forms["auto"] = {"ms_per_step": auto_ms, "queries_per_s": world * n_a / (auto_ms * 1e-3)}
+    # headline: the faster form under the cold-L2 protocol, timed again
+    head = min(("search", "rmi"), key=lambda k: forms[k]["ms_per_step"])
+    head_m = bits.METHOD_SEARCH if head == "search" else bits.METHOD_RMI
+    head_ms, launches, window = timed(count_with(head_m), args.steps, args.warmup)
     db.check()
     clocks = sampler.summary(*window)
-    auto_method = "rmi" if forms["rmi"]["ms_per_step"] < forms["search"]["ms_per_step"] else "search"
+    auto_method = head
     got = counts.cpu().numpy()
     idx = np.random.default_rng(0).choice(n_a, size=256, replace=False)
     oc, _ = o.count_brute(a_np[idx], b_np)
@@ -300,7 +305,7 @@ def run_ours(args):
 
     def e2e_step():
         a_stage.copy_(a_host, non_blocking=True)
-        db.count(a_stage, counts=counts, total=total, check=False)
+        db.count(a_stage, counts=counts, total=total, method=head_m, check=False)
         counts_host.copy_(counts, non_blocking=True)
         total_host.copy_(total, non_blocking=True)
 
@@ -372,6 +377,40 @@ def run_ours(args):
     db4.free()
     del a4, c4
 
+    # ---- all-pairs screen (Sec. 3.3): 64 query sets x 32 databases -------------
+    g5, a5_np, b5_np = bits_synth.config5()
+    t0 = time.time()
+    dbs5 = [bits.Database(to_dev(b5), rmi_leaves_log2=16) for b5 in b5_np]
+    torch.cuda.synchronize()
+    build5_s = time.time() - t0
+    a5 = [to_dev(x) for x in a5_np]
+    m5 = torch.empty((len(a5), len(dbs5)), dtype=torch.uint64, device=dev)
+    bits.count_matrix(dbs5, a5, out=m5)          # autotunes and captures the graph
+    steps5 = max(3, min(args.steps, 5))
+    ms5, l5, _ = timed(lambda: bits.count_matrix(dbs5, a5, out=m5), steps5, 3)
+    m5_np = m5.cpu().numpy()
+    n_q5 = sum(x.shape[0] for x in a5_np)
+    checks = []
+    for (i, j) in ((0, 0), (int(np.argmin([x.shape[0] for x in a5_np])), 31)):
+        t = dbs5[j].count(a5[i], counts=False, method=bits.METHOD_SEARCH)[1]
+        checks.append(int(t.cpu().numpy()[0]) == int(m5_np[i, j]))
+    i_small = int(np.argmin([x.shape[0] for x in a5_np]))
+    bs5, be5 = o.build(b5_np[5])
+    checks.append(o.count_sorted(a5_np[i_small], bs5, be5, want_counts=False)[1] ==
+                  int(m5_np[i_small, 5]))
+    allpairs = {"workload": "64 query sets x 32 databases on the 24-contig genome, sizes "
+                            "log-uniform [1e3, 2e7] (seed 11), lengths U[50,5000], even sets "
+                            "clustered, one learned index per database",
+                "ms_per_step": ms5, "pairs": len(a5) * len(dbs5),
+                "query_database_counts_per_s": world * n_q5 * len(dbs5) / (ms5 * 1e-3),
+                "queries_total": n_q5, "gpu_launches": l5, "build_32_databases_s": build5_s,
+                "parity_sample_ok": bool(all(checks)),
+                "paper_context": "Sec. 3.3: 159 x 159 tracks, about 4e9 intervals per iteration, "
+                                 "9,069 minutes for 1e4 iterations on one 2012 GPU"}
+    for d in dbs5:
+        d.free()
+    del a5, m5
+
     sampler.stop()
 
     # ---- CPU baseline: the oracle as it stands, on a bounded sample -----------
@@ -397,18 +436,19 @@ def run_ours(args):
     # read + 4 B count write + one 32 B sector per search of an array larger
     # than L2 (two searches per query) = 76 B.
     kernel = "k_count_rmi" if auto_method == "rmi" else "k_count_search"
-    achieved = 76.0 * n_a / (auto_ms * 1e-3) / 1e9
+    achieved = 76.0 * n_a / (head_ms * 1e-3) / 1e9
     src = (["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/rmi_search.cuh",
             "paper_1208_3407_b300/csrc/rmi.cu"] if auto_method == "rmi" else
            ["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/count.cu"])
     traffic = profiled_traffic(kernel, src)
     line = {
-        "metric": METRIC, "value": world * n_a / (auto_ms * 1e-3), "unit": "queries/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": auto_ms,
+        "metric": METRIC, "value": world * n_a / (head_ms * 1e-3), "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded generator; the paper's alignment and exon datasets are "
                 "not available)",
-        "config": {"workload": HEADLINE, "method": f"bits_count AUTO (autotuned: {auto_method})",
+        "config": {"workload": HEADLINE,
+                   "method": f"{head} (the faster of plain search and learned index, both timed here)",
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicated database, {world} rank(s), no collective"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -426,6 +466,7 @@ def run_ours(args):
         "parity_sample_ok": parity_ok,
         "mc": mc,
         "scale": scale,
+        "allpairs": allpairs,
     }
     if rank == 0:
         print(json.dumps(line))

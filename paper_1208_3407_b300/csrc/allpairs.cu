@@ -1,11 +1,259 @@
+// All-pairs count matrix (the screen of Sec. 3.3): M[i][j] = total(A_i, B_j)
+// for every query set A_i and database B_j, in one persistent launch.
+//
+// Work is split by query count: a unit is (database j, query set i, chunk of
+// kChunk queries), and units are listed database by database, largest
+// database first, so the deepest (slowest) searches start early and the
+// small units fill the tail.  CTAs take units from an atomic ticket; a CTA
+// reloads its shared-memory top level only when its unit's database differs
+// from the previous one.  Each unit reduces its chunk to one uint64 and adds
+// it to M[i][j] with one atomic.
+//
+// Per database the search method (plain 16-ary tree or learned index) comes
+// from the autotuner, timed on a sample of the queries the first time a size
+// class is seen.  The whole call (zero M, reset the ticket, the persistent
+// launch) is captured once per argument set into a CUDA graph and replayed.
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
 #include "allpairs.cuh"
+#include "count.cuh"
+#include "rmi.cuh"
+#include "rmi_search.cuh"
+#include "search.cuh"
 
 namespace bits {
+namespace {
 
-bits_status run_count_matrix(const bits_db* const*, uint32_t, const uint32_t* const*,
-                             const uint64_t*, uint32_t, uint64_t*, cudaStream_t) {
-  set_error("bits_count_matrix: not built yet");
-  return BITS_ENOTIMPL;
+constexpr int kApBlock = 256;
+constexpr uint32_t kChunk = 8192;
+
+struct MatDb {
+  LevelIndex L;
+  RmiView R;
+  uint32_t nb;
+  int method;
+  uint32_t* err;
+};
+
+struct MatUnit {
+  uint32_t db, set, start, count;
+};
+
+struct MatArgs {
+  const MatDb* dbs;
+  const MatUnit* units;
+  uint32_t n_units;
+  const uint2* const* sets;
+  unsigned long long* matrix;
+  uint32_t n_db;
+  uint32_t* ticket;
+};
+
+__global__ void __launch_bounds__(kApBlock)
+k_allpairs(MatArgs P) {
+  extern __shared__ __align__(16) uint32_t s_top[];
+  __shared__ MatDb s_db;
+  __shared__ uint32_t s_unit;
+  __shared__ int s_cur;
+  __shared__ unsigned long long s_red[32];
+  if (threadIdx.x == 0) s_cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(P.ticket, 1u);
+    __syncthreads();
+    const uint32_t u = s_unit;
+    if (u >= P.n_units) break;
+    const MatUnit U = P.units[u];
+    if ((int)U.db != s_cur) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(P.dbs + U.db);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_db);
+      for (uint32_t k = threadIdx.x; k < sizeof(MatDb) / 4; k += blockDim.x) dst[k] = src[k];
+      __syncthreads();
+      if (s_db.method != BITS_METHOD_RMI) load_top(s_top, s_db.L);
+      if (threadIdx.x == 0) s_cur = (int)U.db;
+      __syncthreads();
+    }
+    const uint2* A = P.sets[U.set] + U.start;
+    const bool rmi = s_db.method == BITS_METHOD_RMI;
+    const uint32_t nb = s_db.nb;
+    unsigned long long acc = 0ull;
+    bool bad = false;
+    for (uint32_t base = 0; base < U.count; base += kApBlock) {
+      const uint32_t i = base + threadIdx.x;
+      const bool valid = i < U.count;
+      uint2 q = make_uint2(0u, 0u);
+      if (valid) q = __ldg(A + i);
+      const uint32_t key_s = q.y, key_e = q.x + 1u;
+      uint32_t rs, re;
+      if (rmi) {
+        rmi_rank2(s_db.R, s_db.L, nb, key_s, key_e, rs, re);
+      } else {
+        top_rank2(s_top, s_db.L.top_size, key_s, key_e, rs, re);
+        quad_descend(s_db.L, rs, key_s, re, key_e);
+      }
+      uint32_t c = icount_from_ranks(rs, re, q.x, nb);
+      if (q.y < q.x) {
+        c = 0u;
+        bad = true;
+      }
+      if (valid) acc += c;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) set_dev_error(s_db.err, DEV_ERR_INVALID);
+    const unsigned long long sum = block_sum_u64(acc, s_red);
+    if (threadIdx.x == 0 && sum) atomicAdd(P.matrix + (size_t)U.set * P.n_db + U.db, sum);
+    __syncthreads();
+  }
+}
+
+int ap_blocks_per_sm(size_t smem) {
+  static int per_sm = 0;
+  static size_t smem_for = 0;
+  if (per_sm == 0 || smem_for != smem) {
+    cudaFuncSetAttribute(k_allpairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_allpairs, kApBlock, smem);
+    per_sm = std::max(1, b);
+    smem_for = smem;
+  }
+  return per_sm;
+}
+
+struct MatGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  void* dev = nullptr;  // descriptors | units | set pointers | ticket
+  uint64_t kernels = 0;
+  ~MatGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (dev) cudaFree(dev);
+  }
+};
+
+std::mutex g_mu;
+std::map<std::vector<uint64_t>, std::shared_ptr<MatGraph>> g_graphs;
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
+                             const uint32_t* const* d_as, const uint64_t* n_as, uint32_t n_sets,
+                             uint64_t* d_matrix, cudaStream_t st) {
+  if (n_db == 0 || n_sets == 0) return BITS_OK;
+  std::vector<uint64_t> key;
+  key.push_back(reinterpret_cast<uintptr_t>(d_matrix));
+  for (uint32_t j = 0; j < n_db; ++j) key.push_back(reinterpret_cast<uintptr_t>(dbs[j]));
+  for (uint32_t i = 0; i < n_sets; ++i) {
+    key.push_back(reinterpret_cast<uintptr_t>(d_as[i]));
+    key.push_back(n_as[i]);
+  }
+  std::shared_ptr<MatGraph> g;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_graphs.find(key);
+    if (it != g_graphs.end()) g = it->second;
+  }
+  if (!g) {
+    // Search method per database: the autotuner, timed on a sample of the
+    // largest query set (at most 2^16 queries).
+    uint32_t big = 0;
+    for (uint32_t i = 1; i < n_sets; ++i)
+      if (n_as[i] > n_as[big]) big = i;
+    const uint32_t n_sample = (uint32_t)std::min<uint64_t>(n_as[big], 1u << 16);
+    std::vector<MatDb> hd(n_db);
+    uint64_t* d_tmp = nullptr;
+    BITS_CUDA_TRY(cudaMallocAsync(&d_tmp, sizeof(uint64_t), st));
+    size_t max_top = 4;
+    for (uint32_t j = 0; j < n_db; ++j) {
+      int m = BITS_METHOD_SEARCH;
+      if (dbs[j]->has_rmi && n_sample) {
+        bits_status s = autotune_count(dbs[j], d_as[big], n_sample, nullptr, d_tmp, st, &m);
+        if (s != BITS_OK) {
+          cudaFreeAsync(d_tmp, st);
+          return s;
+        }
+      }
+      hd[j].L = dbs[j]->lvl;
+      hd[j].R = dbs[j]->has_rmi ? rmi_view(dbs[j]) : RmiView{};
+      hd[j].nb = dbs[j]->n;
+      hd[j].method = m;
+      hd[j].err = dbs[j]->err;
+      if (m != BITS_METHOD_RMI) max_top = std::max<size_t>(max_top, dbs[j]->lvl.top_size);
+    }
+    cudaFreeAsync(d_tmp, st);
+    // Units: largest database first, then set by set, kChunk queries each.
+    std::vector<uint32_t> order(n_db);
+    for (uint32_t j = 0; j < n_db; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return dbs[x]->n > dbs[y]->n; });
+    std::vector<MatUnit> units;
+    for (uint32_t j : order)
+      for (uint32_t i = 0; i < n_sets; ++i)
+        for (uint64_t s0 = 0; s0 < n_as[i]; s0 += kChunk)
+          units.push_back(MatUnit{j, i, (uint32_t)s0,
+                                  (uint32_t)std::min<uint64_t>(kChunk, n_as[i] - s0)});
+    g = std::make_shared<MatGraph>();
+    const size_t off_units = align256(sizeof(MatDb) * n_db);
+    const size_t off_sets = off_units + align256(sizeof(MatUnit) * std::max<size_t>(units.size(), 1));
+    const size_t off_ticket = off_sets + align256(sizeof(void*) * n_sets);
+    BITS_CUDA_TRY(cudaMalloc(&g->dev, off_ticket + 256));
+    char* base = static_cast<char*>(g->dev);
+    std::vector<const void*> sets(d_as, d_as + n_sets);
+    BITS_CUDA_TRY(cudaMemcpy(base, hd.data(), sizeof(MatDb) * n_db, cudaMemcpyHostToDevice));
+    if (!units.empty())
+      BITS_CUDA_TRY(cudaMemcpy(base + off_units, units.data(), sizeof(MatUnit) * units.size(),
+                               cudaMemcpyHostToDevice));
+    BITS_CUDA_TRY(cudaMemcpy(base + off_sets, sets.data(), sizeof(void*) * n_sets,
+                             cudaMemcpyHostToDevice));
+    MatArgs P{};
+    P.dbs = reinterpret_cast<const MatDb*>(base);
+    P.units = reinterpret_cast<const MatUnit*>(base + off_units);
+    P.n_units = (uint32_t)units.size();
+    P.sets = reinterpret_cast<const uint2* const*>(base + off_sets);
+    P.matrix = reinterpret_cast<unsigned long long*>(d_matrix);
+    P.n_db = n_db;
+    P.ticket = reinterpret_cast<uint32_t*>(base + off_ticket);
+    const size_t smem = sizeof(uint32_t) * 2 * max_top;
+    const uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(P.n_units, 1),
+                                             (uint32_t)(ap_blocks_per_sm(smem) * sm_count()));
+
+    cudaStream_t cap = nullptr;
+    BITS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return cuda_status(e, "cudaStreamBeginCapture");
+    }
+    cudaMemsetAsync(d_matrix, 0, sizeof(uint64_t) * (size_t)n_sets * n_db, cap);
+    cudaMemsetAsync(P.ticket, 0, sizeof(uint32_t), cap);
+    k_allpairs<<<grid, kApBlock, smem, cap>>>(P);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture(count_matrix)");
+    g->graph = graph;
+    BITS_CUDA_TRY(cudaGraphInstantiate(&g->exec, graph, 0));
+    g->kernels = 1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_graphs[key] = g;
+  }
+  BITS_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+  count_launch((uint32_t)g->kernels);
+  return BITS_OK;
+}
+
+void release_matrix_graphs(const bits_db* db) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+    bool uses = false;
+    for (size_t k = 1; k < it->first.size(); ++k)
+      if (it->first[k] == reinterpret_cast<uintptr_t>(db)) uses = true;
+    it = uses ? g_graphs.erase(it) : std::next(it);
+  }
 }
 
 }  // namespace bits

@@ -10,4 +10,7 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
                              const uint32_t* const* d_as, const uint64_t* n_as, uint32_t n_sets,
                              uint64_t* d_matrix, cudaStream_t st);
 
+// Forget the cached all-pairs graphs that use `db` (called by bits_free).
+void release_matrix_graphs(const bits_db* db);
+
 }  // namespace bits

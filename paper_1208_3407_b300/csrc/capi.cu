@@ -330,6 +330,7 @@ void bits_free(bits_db* db) {
   cudaGetDevice(&prev);
   if (prev != db->device) cudaSetDevice(db->device);
   release_mc_graphs(db);
+  release_matrix_graphs(db);
   cudaFree(db->block);
   if (prev != db->device) cudaSetDevice(prev);
   delete db;

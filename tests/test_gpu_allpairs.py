@@ -1,0 +1,96 @@
+"""Parity of the all-pairs count matrix (the screen of Sec. 3.3) with the oracle.
+
+M[i][j] = total(A_i, B_j) from one persistent launch must equal the oracle's
+Algorithm 2 total for every pair (bit-exact, uint64).
+"""
+import numpy as np
+import pytest
+import torch
+
+import bits_synth as synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+O = oracle.get()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.uint32)).cuda()
+
+
+@pytest.fixture(scope="module")
+def bits():
+    import paper_1208_3407_b300 as bits
+    return bits
+
+
+def oracle_matrix(a_sets, b_sets):
+    built = [O.build(b) for b in b_sets]
+    m = np.zeros((len(a_sets), len(b_sets)), np.uint64)
+    for i, a in enumerate(a_sets):
+        for j, (bs, be) in enumerate(built):
+            m[i, j] = O.count_sorted(a, bs, be, threads=8, want_counts=False)[1]
+    return m
+
+
+@pytest.mark.parametrize("leaves", [0, 12])
+def test_reduced_screen(bits, leaves):
+    genome, a_sets, b_sets = synth.config5(n_sets_a=8, n_sets_b=6, hi=200_000)
+    dbs = [bits.Database(dev(b), rmi_leaves_log2=leaves) for b in b_sets]
+    m = bits.count_matrix(dbs, [dev(a) for a in a_sets])
+    np.testing.assert_array_equal(m.cpu().numpy(), oracle_matrix(a_sets, b_sets))
+    for d in dbs:
+        d.free()
+
+
+def test_mixed_databases_and_empty_sets(bits):
+    genome, a_sets, b_sets = synth.config5(n_sets_a=5, n_sets_b=4, hi=50_000, seed=21)
+    a_sets = a_sets + [np.zeros((0, 2), np.uint32), a_sets[0][:1]]
+    b_sets = b_sets + [b_sets[1][:1], np.zeros((0, 2), np.uint32)]
+    dbs = [bits.Database(dev(b), rmi_leaves_log2=(10 if j % 2 else 0))
+           for j, b in enumerate(b_sets)]
+    m = bits.count_matrix(dbs, [dev(a) for a in a_sets])
+    np.testing.assert_array_equal(m.cpu().numpy(), oracle_matrix(a_sets, b_sets))
+    for d in dbs:
+        d.free()
+
+
+def test_graph_replay_and_changed_contents(bits):
+    genome, a_sets, b_sets = synth.config5(n_sets_a=4, n_sets_b=3, hi=80_000, seed=22)
+    dbs = [bits.Database(dev(b)) for b in b_sets]
+    da = [dev(a) for a in a_sets]
+    out = torch.empty((4, 3), dtype=torch.uint64, device="cuda")
+    m1 = bits.count_matrix(dbs, da, out=out).cpu().numpy().copy()
+    m2 = bits.count_matrix(dbs, da, out=out).cpu().numpy().copy()
+    np.testing.assert_array_equal(m1, m2)
+    np.testing.assert_array_equal(m1, oracle_matrix(a_sets, b_sets))
+    shifted = a_sets[2] + np.uint32(777)
+    da[2].copy_(dev(shifted))
+    m3 = bits.count_matrix(dbs, da, out=out).cpu().numpy()
+    a_sets[2] = shifted
+    np.testing.assert_array_equal(m3, oracle_matrix(a_sets, b_sets))
+    for d in dbs:
+        d.free()
+
+
+def test_full_screen_64_by_32(bits):
+    """The full 64 x 32 screen (sizes log-uniform in [1e3, 2e7]): every entry
+    equals the single-database count of that pair; the oracle recomputes the
+    pairs of the four smallest query sets against four databases."""
+    genome, a_sets, b_sets = synth.config5()
+    dbs = [bits.Database(dev(b), rmi_leaves_log2=16) for b in b_sets]
+    da = [dev(a) for a in a_sets]
+    m = bits.count_matrix(dbs, da).cpu().numpy()
+    per_pair = np.zeros_like(m)
+    for j, d in enumerate(dbs):
+        for i, a in enumerate(da):
+            per_pair[i, j] = int(d.count(a, counts=False, method=bits.METHOD_SEARCH)[1].cpu().numpy()[0])
+    np.testing.assert_array_equal(m, per_pair)
+    small = np.argsort([a.shape[0] for a in a_sets])[:4]
+    for j in (0, 7, 19, 31):
+        bs, be = O.build(b_sets[j])
+        for i in small:
+            assert m[i, j] == O.count_sorted(a_sets[i], bs, be, want_counts=False)[1]
+    for d in dbs:
+        d.free()
