@@ -1,8 +1,9 @@
 // Method choice for BITS_METHOD_AUTO.
 //
 // The first AUTO count of a size class -- (device, ceil log2 |A|, ceil log2
-// |B|, learned index built or not) -- times every method the database has
-// (plain search, learned index) on the caller's own inputs with CUDA events,
+// |B|, learned index built or not, per-query counts wanted or not) -- times every method the database has
+// (plain search, learned index, merge path when the query set is at least
+// 1/16 of the database) on the caller's own inputs with CUDA events,
 // three runs each after one warm-up, and keeps the fastest.  Later calls of
 // the class reuse the choice.  When BITS_AUTOTUNE_CACHE names a file, choices
 // are read from it at first use and appended to it as they are made.  Under
@@ -14,8 +15,10 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "count.cuh"
+#include "mergepath.cuh"
 #include "rmi.cuh"
 
 namespace bits {
@@ -69,8 +72,15 @@ void save_choice(const Key& k, int m) {
 
 bits_status run_method(const bits_db* db, int m, const uint32_t* d_a, uint32_t n,
                        uint32_t* d_counts, uint64_t* d_total, cudaStream_t st) {
-  return m == BITS_METHOD_RMI ? launch_count_rmi(db, d_a, n, d_counts, d_total, st)
-                              : launch_count_search(db, d_a, n, d_counts, d_total, st);
+  if (m == BITS_METHOD_RMI) return launch_count_rmi(db, d_a, n, d_counts, d_total, st);
+  if (m == BITS_METHOD_MERGEPATH) return launch_count_mergepath(db, d_a, n, d_counts, d_total, st);
+  return launch_count_search(db, d_a, n, d_counts, d_total, st);
+}
+
+// Merge path streams all of B per call, so it is only a candidate when the
+// query set is at least 1/16 of the database.
+bool mergepath_candidate(const bits_db* db, uint32_t n) {
+  return n < (1u << 31) && (uint64_t)n * 16 >= db->n;
 }
 
 }  // namespace
@@ -79,13 +89,18 @@ int choose_count_method(const bits_db* db, uint32_t n) {
   const int fallback = db->has_rmi ? BITS_METHOD_RMI : BITS_METHOD_SEARCH;
   std::lock_guard<std::mutex> lk(g_mu);
   load_cache();
-  auto it = g_choice.find(Key(device_name(), ceil_log2(n), ceil_log2(db->n), db->has_rmi));
+  auto it = g_choice.find(Key(device_name(), ceil_log2(n), ceil_log2(db->n),
+                             (db->has_rmi ? 1 : 0) | 2));
   return it == g_choice.end() ? fallback : it->second;
 }
 
 bits_status autotune_count(const bits_db* db, const uint32_t* d_a, uint32_t n,
                            uint32_t* d_counts, uint64_t* d_total, cudaStream_t st, int* method) {
-  const Key key(device_name(), ceil_log2(n), ceil_log2(db->n), db->has_rmi);
+  const Key key(device_name(), ceil_log2(n), ceil_log2(db->n),
+                (db->has_rmi ? 1 : 0) | (d_counts ? 2 : 0));
+  std::vector<int> cands = {BITS_METHOD_SEARCH};
+  if (db->has_rmi) cands.push_back(BITS_METHOD_RMI);
+  if (mergepath_candidate(db, n)) cands.push_back(BITS_METHOD_MERGEPATH);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_cache();
@@ -98,9 +113,8 @@ bits_status autotune_count(const bits_db* db, const uint32_t* d_a, uint32_t n,
   *method = db->has_rmi ? BITS_METHOD_RMI : BITS_METHOD_SEARCH;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   BITS_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-  if (cs != cudaStreamCaptureStatusNone || !db->has_rmi || n == 0) return BITS_OK;
+  if (cs != cudaStreamCaptureStatusNone || cands.size() < 2 || n == 0) return BITS_OK;
 
-  const int cands[2] = {BITS_METHOD_SEARCH, BITS_METHOD_RMI};
   float best = 1e30f;
   int best_m = *method;
   cudaEvent_t e0, e1;
@@ -111,13 +125,13 @@ bits_status autotune_count(const bits_db* db, const uint32_t* d_a, uint32_t n,
     if (s != BITS_OK) return s;
     float tot = 0.f;
     for (int r = 0; r < 3; ++r) {
-      cudaEventRecord(e0, st);
+      BITS_CUDA_TRY(cudaEventRecord(e0, st));
       s = run_method(db, m, d_a, n, d_counts, d_total, st);
       if (s != BITS_OK) return s;
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
+      BITS_CUDA_TRY(cudaEventRecord(e1, st));
+      BITS_CUDA_TRY(cudaEventSynchronize(e1));
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      BITS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
       tot += ms;
     }
     if (tot < best) {

@@ -151,7 +151,7 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
     RadixScratch ws{};
     const size_t sw = radix_status_words(nn);
     const size_t scratch_bytes = 2 * align_up(sizeof(uint32_t) * nn, 256) +
-                                 align_up(sizeof(uint32_t) * 2048, 256) +
+                                 align_up(sizeof(uint32_t) * kRadixHistWords, 256) +
                                  align_up(sizeof(uint32_t) * sw * 8, 256) + 256;
     void* scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, st);
@@ -162,7 +162,7 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
     ws.tmp_e = reinterpret_cast<uint32_t*>(sb);
     sb += align_up(sizeof(uint32_t) * nn, 256);
     ws.hist = reinterpret_cast<uint32_t*>(sb);
-    sb += align_up(sizeof(uint32_t) * 2048, 256);
+    sb += align_up(sizeof(uint32_t) * kRadixHistWords, 256);
     ws.status = reinterpret_cast<uint32_t*>(sb);
     sb += align_up(sizeof(uint32_t) * sw * 8, 256);
     ws.tickets = reinterpret_cast<uint32_t*>(sb);

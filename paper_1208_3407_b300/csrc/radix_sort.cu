@@ -1,25 +1,30 @@
-// LSD radix sort of the interval starts and ends (Algorithm 2's two Sort
-// steps; Sec. 2.4 relies on a GPU radix sort for them).
+// LSD radix sort of interval starts and ends (Algorithm 2's two Sort steps;
+// Sec. 2.4 relies on a GPU radix sort for them), keys only or key/value.
 //
 // Design (one GPU, HBM-bound):
-//   * k_radix_hist reads the array-of-structures input once, validates
-//     start < end, and builds all four 8-bit digit histograms of both the
-//     start and the end keys (8 x 256 counters).
-//   * k_onesweep runs one digit pass for both arrays in one launch.  A tile
-//     of 8192 keys is ranked stably inside the CTA (warp match-any per key),
-//     its per-digit counts are published to a decoupled look-back table, the
-//     CTA gathers the exclusive prefix of earlier tiles from that table and
-//     scatters its keys, staged in digit order in shared memory so that
-//     stores of one digit are contiguous.  The first pass reads the start or
-//     end word straight out of the interval array, so there is no separate
-//     split step.  Tiles take ticket numbers in launch order, so a tile waits
-//     only on tiles that already run; every wait is bounded and reports
-//     DEV_ERR_TIMEOUT instead of hanging.
+//   * k_radix_hist reads the interval array once, validates it, and builds
+//     all four 8-bit digit histograms of the two keys it derives from every
+//     interval (each the start or the end word, plus a constant, exactly as
+//     the first pass derives them).
+//   * k_onesweep runs one digit pass for both key arrays in one launch.  A
+//     tile of 8192 keys is ranked stably inside the CTA (bit-sliced ballots
+//     and per-warp shared-memory counters), its per-digit counts are published to a decoupled look-back
+//     table, and the CTA gathers the exclusive prefix of earlier tiles from
+//     that table: one thread per digit reads eight predecessor tiles per
+//     round trip and stops at the nearest tile that has published its
+//     inclusive prefix.  Keys (and values) are staged in digit order in
+//     shared memory so that stores of one digit are contiguous.  The first
+//     pass reads its key straight out of the interval array, so there is no
+//     separate split step; in key/value mode the first pass's value is the
+//     interval's index (top bit set if the interval is inverted).  Tiles
+//     take ticket numbers in launch order, so a tile only waits on tiles
+//     that already run; every wait is bounded and reports DEV_ERR_TIMEOUT.
 //   * Passes whose digit is the same for every key are skipped (the host
 //     reads the histograms once, together with the validation flag).
 //
-// Traffic per key: 8 B (histogram read of the pair, shared by both arrays)
-// + passes x (4 B read + 4 B write), plus 8 B/key of first-pass pair reads.
+// Traffic per key: 8 B pair read for the histogram (shared by both arrays),
+// 8 B pair read in the first pass, then passes x (4 B read + 4 B write),
+// doubled for values.
 #include "common.cuh"
 #include "radix_sort.cuh"
 
@@ -33,37 +38,50 @@ constexpr int kSwBlock = 512;
 constexpr int kSwWarps = kSwBlock / 32;
 constexpr int kSwKpt = 16;
 constexpr int kSwTile = kSwBlock * kSwKpt;  // 8192 keys
+constexpr int kLookAhead = 8;  // predecessor status words read per round trip
+constexpr int kCnt = kRadix + 1;  // per-warp counters: 256 digits + the tail's empty lanes
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kValMask = (1u << 30) - 1;
 
+// validate: 0 = database (end > start required, else DEV_ERR_INVALID),
+//           1 = queries (end < start sets *inv, not an error here).
 __global__ void __launch_bounds__(kHistBlock)
-k_radix_hist(const uint2* __restrict__ b, uint32_t n, uint32_t* __restrict__ hist,
-             uint32_t* __restrict__ err) {
+k_radix_hist(const uint2* __restrict__ b, uint32_t n, int comp0, uint32_t add0, int comp1,
+             uint32_t add1, int validate, uint32_t* __restrict__ hist, uint32_t* __restrict__ err,
+             uint32_t* __restrict__ inv) {
   __shared__ uint32_t sh[2 * kPasses * kRadix];
   for (int i = threadIdx.x; i < 2 * kPasses * kRadix; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   bool bad = false;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint2 v = b[i];
-    bad |= !(v.x < v.y);
+    bad |= validate ? (v.y < v.x) : !(v.x < v.y);
+    const uint32_t k0 = (comp0 ? v.y : v.x) + add0, k1 = (comp1 ? v.y : v.x) + add1;
     #pragma unroll
     for (int p = 0; p < kPasses; ++p) {
-      atomicAdd(&sh[p * kRadix + ((v.x >> (8 * p)) & 255u)], 1u);
-      atomicAdd(&sh[(kPasses + p) * kRadix + ((v.y >> (8 * p)) & 255u)], 1u);
+      atomicAdd(&sh[p * kRadix + ((k0 >> (8 * p)) & 255u)], 1u);
+      atomicAdd(&sh[(kPasses + p) * kRadix + ((k1 >> (8 * p)) & 255u)], 1u);
     }
   }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) set_dev_error(err, DEV_ERR_INVALID);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) {
+    if (validate) atomicOr(inv, 1u);
+    else set_dev_error(err, DEV_ERR_INVALID);
+  }
   for (int i = threadIdx.x; i < 2 * kPasses * kRadix; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
 struct SweepJob {
-  const uint32_t* in;  // keys of the previous pass, or NULL on the first pass
-  const uint2* aos;    // interval pairs (first pass)
-  uint32_t* out;
-  const uint32_t* hist;  // [256] digit histogram of this pass
-  uint32_t* status;      // [tiles][256] look-back words, zeroed
-  uint32_t* ticket;      // zeroed
-  int comp;              // 0: start word, 1: end word
+  const uint32_t* in_keys;  // keys of the previous pass, or NULL on the first pass
+  const uint32_t* in_vals;  // values of the previous pass (key/value mode)
+  const uint2* aos;         // interval pairs (first pass)
+  uint32_t* out_keys;
+  uint32_t* out_vals;
+  const uint32_t* hist;     // [256] digit histogram of this pass
+  uint32_t* status;         // [tiles][256] look-back words, zeroed
+  uint32_t* ticket;         // zeroed
+  int comp;                 // first pass: 0 = start word, 1 = end word
+  uint32_t add;             // first pass: constant added to the word
+  int flag_inv;             // first pass: mark inverted intervals in the value
   int shift;
 };
 struct SweepJobs {
@@ -97,34 +115,43 @@ __device__ __forceinline__ uint32_t scan256_excl(uint32_t v, uint32_t* s_w) {
   return r;
 }
 
+template <bool KV>
 __global__ void __launch_bounds__(kSwBlock, 2)
 k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
-  __shared__ uint32_t s_stage[kSwTile];
-  __shared__ uint16_t s_wcnt[kSwWarps][kRadix];
-  __shared__ uint32_t s_tstart[kRadix];
-  __shared__ uint32_t s_gbase[kRadix];
-  __shared__ uint32_t s_w[kRadix / 32];
-  __shared__ uint32_t s_tile;
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* s_stage = sm;
+  uint32_t* s_vstage = sm + kSwTile;  // key/value mode only
+  uint32_t* s_wcnt = sm + (KV ? 2 : 1) * kSwTile;  // [warps][kCnt]: per-warp digit counters
+  uint32_t* s_tstart = s_wcnt + kSwWarps * kCnt;
+  uint32_t* s_gbase = s_tstart + kRadix;
+  uint32_t* s_tcount = s_gbase + kRadix;
+  uint32_t* s_dbase = s_tcount + kRadix;
+  uint32_t* s_w = s_dbase + kRadix;
+  uint32_t* s_tile = s_w + kRadix / 32;
 
   const bool y1 = blockIdx.y != 0;
-  const uint32_t* in = y1 ? jobs.j[1].in : jobs.j[0].in;
-  const uint2* aos = y1 ? jobs.j[1].aos : jobs.j[0].aos;
-  uint32_t* out = y1 ? jobs.j[1].out : jobs.j[0].out;
-  const uint32_t* hist = y1 ? jobs.j[1].hist : jobs.j[0].hist;
-  uint32_t* status = y1 ? jobs.j[1].status : jobs.j[0].status;
-  uint32_t* ticket = y1 ? jobs.j[1].ticket : jobs.j[0].ticket;
-  const int comp = y1 ? jobs.j[1].comp : jobs.j[0].comp;
-  const int shift = y1 ? jobs.j[1].shift : jobs.j[0].shift;
+  const SweepJob& J0 = jobs.j[0];
+  const SweepJob& J1 = jobs.j[1];
+  const uint32_t* in_keys = y1 ? J1.in_keys : J0.in_keys;
+  const uint32_t* in_vals = y1 ? J1.in_vals : J0.in_vals;
+  const uint2* aos = y1 ? J1.aos : J0.aos;
+  uint32_t* out_keys = y1 ? J1.out_keys : J0.out_keys;
+  uint32_t* out_vals = y1 ? J1.out_vals : J0.out_vals;
+  const uint32_t* hist = y1 ? J1.hist : J0.hist;
+  uint32_t* status = y1 ? J1.status : J0.status;
+  uint32_t* ticket = y1 ? J1.ticket : J0.ticket;
+  const int comp = y1 ? J1.comp : J0.comp;
+  const uint32_t add = y1 ? J1.add : J0.add;
+  const int flag_inv = y1 ? J1.flag_inv : J0.flag_inv;
+  const int shift = y1 ? J1.shift : J0.shift;
 
   const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
-  {
-    uint32_t* z = reinterpret_cast<uint32_t*>(&s_wcnt[0][0]);
-    for (int i = tid; i < kSwWarps * kRadix / 2; i += kSwBlock) z[i] = 0u;
-  }
+  if (tid == 0) *s_tile = atomicAdd(ticket, 1u);
+  for (int i = tid; i < kSwWarps * kCnt; i += kSwBlock) s_wcnt[i] = 0u;
   const uint32_t hcount = tid < kRadix ? hist[tid] : 0u;
-  const uint32_t dbase = scan256_excl(hcount, s_w);  // also syncs s_tile / s_wcnt
-  const uint32_t tile = s_tile;
+  const uint32_t dbase = scan256_excl(hcount, s_w);  // also publishes *s_tile / s_wcnt
+  if (tid < kRadix) s_dbase[tid] = dbase;
+  const uint32_t tile = *s_tile;
   const uint32_t tile_base = tile * (uint32_t)kSwTile;
   const uint32_t warp_base = tile_base + w * 32u * kSwKpt;
 
@@ -134,38 +161,52 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
     const uint32_t idx = warp_base + k * 32u + lane;
     uint32_t v = 0u;
     if (idx < n) {
-      if (in) {
-        v = in[idx];
+      if (in_keys) {
+        v = in_keys[idx];
       } else {
         const uint2 p = aos[idx];
-        v = comp ? p.y : p.x;
+        v = (comp ? p.y : p.x) + add;
       }
     }
     key[k] = v;
   }
 
   // Stable rank of every key among the keys of its warp with the same digit
-  // (< 32 * kSwKpt, so two 16-bit ranks share a register).
+  // (< 32 * kSwKpt, so two 16-bit ranks share a register).  The lanes that
+  // share a digit come from eight bit-sliced ballots (a ninth separates the
+  // tail's empty lanes, which use digit 256); the lowest of them adds their
+  // number to the warp's counter with one shared-memory atomic and passes
+  // the old value on.  The atomics of one warp are performed in program
+  // order, so ranks follow key order within the warp.
   uint32_t rank2[kSwKpt / 2];
   #pragma unroll
   for (int k = 0; k < kSwKpt / 2; ++k) rank2[k] = 0u;
   #pragma unroll
-  for (int k = 0; k < kSwKpt; ++k) {
-    const uint32_t idx = warp_base + k * 32u + lane;
-    const bool valid = idx < n;
-    const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid);
-    const uint32_t d = (key[k] >> shift) & 255u;
-    if (valid) {
-      const unsigned peers = __match_any_sync(vmask, d);
-      const int leader = __ffs(peers) - 1;
-      uint32_t base = 0u;
-      if ((int)lane == leader) {
-        base = s_wcnt[w][d];
-        s_wcnt[w][d] = (uint16_t)(base + __popc(peers));
+  for (int h = 0; h < 2; ++h) {
+    constexpr int kH = kSwKpt / 2;
+    uint32_t lead_base[kH];
+    unsigned peers_k[kH];
+    #pragma unroll
+    for (int kk = 0; kk < kH; ++kk) {
+      const int k = h * kH + kk;
+      const uint32_t idx = warp_base + k * 32u + lane;
+      const uint32_t d = idx < n ? ((key[k] >> shift) & 255u) : 256u;
+      unsigned peers = 0xFFFFFFFFu;
+      #pragma unroll
+      for (int b = 0; b < 9; ++b) {
+        const unsigned bb = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bb : ~bb;
       }
-      base = __shfl_sync(vmask, base, leader);
-      __syncwarp(vmask);
-      rank2[k / 2] |= (base + __popc(peers & lanemask_lt())) << (16 * (k & 1));
+      peers_k[kk] = peers;
+      lead_base[kk] = 0u;
+      if ((int)lane == __ffs(peers) - 1)
+        lead_base[kk] = atomicAdd(s_wcnt + w * kCnt + d, (unsigned)__popc(peers));
+    }
+    #pragma unroll
+    for (int kk = 0; kk < kH; ++kk) {
+      const int k = h * kH + kk;
+      const uint32_t base = __shfl_sync(0xFFFFFFFFu, lead_base[kk], __ffs(peers_k[kk]) - 1);
+      rank2[k / 2] |= (base + __popc(peers_k[kk] & lanemask_lt())) << (16 * (k & 1));
     }
   }
   __syncthreads();
@@ -175,54 +216,89 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
   if (tid < kRadix) {
     #pragma unroll
     for (int ww = 0; ww < kSwWarps; ++ww) {
-      const uint32_t c = s_wcnt[ww][tid];
-      s_wcnt[ww][tid] = (uint16_t)tcount;
+      const uint32_t c = s_wcnt[ww * kCnt + tid];
+      s_wcnt[ww * kCnt + tid] = tcount;
       tcount += c;
     }
+    s_tcount[tid] = tcount;
     // Publish this tile's count as early as possible.
     volatile uint32_t* st = status + (size_t)tile * kRadix + tid;
     *st = (tile == 0 ? kFlagPre : kFlagAgg) | tcount;
   }
   const uint32_t tstart = scan256_excl(tcount, s_w);
-  if (tid < kRadix) s_tstart[tid] = tstart;
+  if (tid < kRadix) {
+    s_tstart[tid] = tstart;
+    if (tile == 0) s_gbase[tid] = dbase - tstart;
+  }
   __syncthreads();
 
-  // Stage the tile's keys in digit order.
+  // Stage the tile's keys (and values) in digit order.
   #pragma unroll
   for (int k = 0; k < kSwKpt; ++k) {
     const uint32_t idx = warp_base + k * 32u + lane;
     if (idx < n) {
       const uint32_t d = (key[k] >> shift) & 255u;
       const uint32_t r = (rank2[k / 2] >> (16 * (k & 1))) & 0xFFFFu;
-      const uint32_t at = s_tstart[d] + s_wcnt[w][d] + r;
-      if (at < (uint32_t)kSwTile) s_stage[at] = key[k];
+      const uint32_t at = s_tstart[d] + s_wcnt[w * kCnt + d] + r;
+      if (at < (uint32_t)kSwTile) {
+        s_stage[at] = key[k];
+        if (KV) {
+          uint32_t v;
+          if (in_keys) {
+            v = in_vals[idx];
+          } else {
+            v = idx;
+            if (flag_inv) {
+              const uint2 p = aos[idx];
+              if (p.y < p.x) v |= 0x80000000u;
+            }
+          }
+          s_vstage[at] = v;
+        }
+      }
     }
   }
 
-  // Decoupled look-back: exclusive prefix of this digit over earlier tiles.
-  if (tid < kRadix) {
-    uint32_t excl = 0u;
-    if (tile > 0) {
-      uint32_t t = tile - 1, spins = 0;
-      while (true) {
-        const uint32_t v = *(volatile const uint32_t*)(status + (size_t)t * kRadix + tid);
-        const uint32_t flag = v & ~kValMask;
-        if (flag == 0u) {
-          if (++spins > kSpinLimit) {
-            set_dev_error(err, DEV_ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(100);
+  // Decoupled look-back, one thread per digit, eight predecessors per round
+  // trip: their status words are loaded together, then consumed nearest
+  // first until a tile with its inclusive prefix is reached.
+  if (tile > 0 && tid < kRadix) {
+    uint32_t excl = 0u, spins = 0u;
+    int hi = (int)tile;  // next predecessor to consume is hi - 1
+    bool done = false;
+    while (!done) {
+      uint32_t v[kLookAhead];
+      #pragma unroll
+      for (int k = 0; k < kLookAhead; ++k) {
+        const int t = hi - 1 - k;
+        v[k] = t >= 0 ? *(volatile const uint32_t*)(status + (size_t)t * kRadix + tid) : kFlagPre;
+      }
+      int used = 0;
+      bool stalled = false;
+      #pragma unroll
+      for (int k = 0; k < kLookAhead; ++k) {
+        if (done || stalled) continue;
+        const uint32_t fl = v[k] & ~kValMask;
+        if (fl == 0u) {
+          stalled = true;
           continue;
         }
-        excl += v & kValMask;
-        if (flag == kFlagPre || t == 0) break;
-        --t;
+        excl += v[k] & kValMask;
+        ++used;
+        if (fl == kFlagPre) done = true;
       }
-      volatile uint32_t* st = status + (size_t)tile * kRadix + tid;
-      *st = kFlagPre | ((excl + tcount) & kValMask);
+      hi -= used;
+      if (!done && stalled) {
+        if (++spins > kSpinLimit) {
+          set_dev_error(err, DEV_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
     }
     s_gbase[tid] = dbase + excl - tstart;
+    volatile uint32_t* st = status + (size_t)tile * kRadix + tid;
+    *st = kFlagPre | ((excl + tcount) & kValMask);
   }
   __syncthreads();
 
@@ -231,10 +307,29 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
   for (uint32_t i = tid; i < valid_here; i += kSwBlock) {
     const uint32_t v = s_stage[i];
     const uint32_t at = s_gbase[(v >> shift) & 255u] + i;
-    if (at < n) out[at] = v;
-    else oob = true;
+    if (at < n) {
+      out_keys[at] = v;
+      if (KV) out_vals[at] = s_vstage[i];
+    } else {
+      oob = true;
+    }
   }
   if (oob) set_dev_error(err, DEV_ERR_TIMEOUT);
+}
+
+size_t sweep_smem(bool kv) {
+  return sizeof(uint32_t) *
+         ((kv ? 2 : 1) * kSwTile + kSwWarps * kCnt + 5 * kRadix + kRadix / 32 + 4);
+}
+
+template <bool KV>
+void prepare_sweep() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_onesweep<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sweep_smem(KV));
+    done = true;
+  }
 }
 
 }  // namespace
@@ -244,28 +339,36 @@ size_t radix_status_words(uint32_t n) {
   return (size_t)tiles * kRadix;
 }
 
-bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, uint32_t* out_e,
-                                 uint32_t* d_err, RadixScratch& ws, cudaStream_t st) {
+bits_status radix_sort_pairs(const uint2* d_src, uint32_t n, const SortSpec spec[2], int validate,
+                             uint32_t* d_err, RadixScratch& ws, cudaStream_t st,
+                             bool* any_inverted) {
+  if (any_inverted) *any_inverted = false;
   if (n == 0) return BITS_OK;
+  const bool kv = spec[0].out_vals != nullptr;
   const uint32_t tiles = (n + kSwTile - 1) / kSwTile;
   const size_t status_words = (size_t)tiles * kRadix;
 
-  BITS_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * 2 * kPasses * kRadix, st));
+  BITS_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, sizeof(uint32_t) * (2 * kPasses * kRadix + 1), st));
+  uint32_t* d_inv = ws.hist + 2 * kPasses * kRadix;
   const int hist_grid = std::max(1, std::min<int>(sm_count() * 4, (n + kHistBlock - 1) / kHistBlock));
-  k_radix_hist<<<hist_grid, kHistBlock, 0, st>>>(d_b, n, ws.hist, d_err);
+  k_radix_hist<<<hist_grid, kHistBlock, 0, st>>>(d_src, n, spec[0].comp, spec[0].add,
+                                                 spec[1].comp, spec[1].add, validate, ws.hist,
+                                                 d_err, d_inv);
   BITS_LAUNCH_CHECK("k_radix_hist");
 
-  uint32_t h_hist[2 * kPasses * kRadix];
+  uint32_t h_hist[2 * kPasses * kRadix + 1];
   uint32_t h_err = 0;
   BITS_CUDA_TRY(cudaMemcpyAsync(h_hist, ws.hist, sizeof(h_hist), cudaMemcpyDeviceToHost, st));
   BITS_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   BITS_CUDA_TRY(cudaStreamSynchronize(st));
-  if (h_err & DEV_ERR_INVALID) {
+  if (!validate && (h_err & DEV_ERR_INVALID)) {
     set_error("bits_build_db: a database interval has end <= start");
     return BITS_EINVAL;
   }
+  if (any_inverted) *any_inverted = h_hist[2 * kPasses * kRadix] != 0;
 
   // Active passes per array: a pass whose digit is constant keeps the order.
+  // Every array keeps at least one pass, which moves it out of the pairs.
   int passes[2][kPasses], np[2] = {0, 0};
   for (int a = 0; a < 2; ++a) {
     for (int p = 0; p < kPasses; ++p) {
@@ -274,43 +377,58 @@ bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, 
         if (h_hist[(a * kPasses + p) * kRadix + d] == n) constant = true;
       if (!constant) passes[a][np[a]++] = p;
     }
-    if (np[a] == 0) passes[a][np[a]++] = 0;  // still split the keys out of the pairs
+    if (np[a] == 0) passes[a][np[a]++] = 0;
   }
   const int steps = std::max(np[0], np[1]);
   BITS_CUDA_TRY(cudaMemsetAsync(ws.status, 0, sizeof(uint32_t) * status_words * 2 * steps, st));
   BITS_CUDA_TRY(cudaMemsetAsync(ws.tickets, 0, sizeof(uint32_t) * 2 * kPasses, st));
+  if (kv) prepare_sweep<true>();
+  else prepare_sweep<false>();
 
-  uint32_t* final_out[2] = {out_s, out_e};
-  uint32_t* tmp[2] = {ws.tmp_s, ws.tmp_e};
-  const uint32_t* cur[2] = {nullptr, nullptr};
+  const uint32_t* cur_k[2] = {nullptr, nullptr};
+  const uint32_t* cur_v[2] = {nullptr, nullptr};
   for (int step = 0; step < steps; ++step) {
     SweepJobs jobs{};
     int nj = 0;
-    int job_array[2] = {-1, -1};
     for (int a = 0; a < 2; ++a) {
       if (step >= np[a]) continue;
-      // Ping-pong so that the array's last active pass lands in final_out.
-      const int remaining = np[a] - 1 - step;
-      uint32_t* dst = (remaining % 2 == 0) ? final_out[a] : tmp[a];
+      // Ping-pong so that the array's last active pass lands in the output.
+      const bool to_out = (np[a] - 1 - step) % 2 == 0;
       SweepJob& J = jobs.j[nj];
-      J.in = cur[a];
-      J.aos = d_b;
-      J.comp = a;
-      J.out = dst;
+      J.in_keys = cur_k[a];
+      J.in_vals = cur_v[a];
+      J.aos = d_src;
+      J.out_keys = to_out ? spec[a].out_keys : spec[a].tmp_keys;
+      J.out_vals = to_out ? spec[a].out_vals : spec[a].tmp_vals;
       J.hist = ws.hist + (a * kPasses + passes[a][step]) * kRadix;
       J.status = ws.status + status_words * (size_t)(2 * step + a);
       J.ticket = ws.tickets + 2 * step + a;
+      J.comp = spec[a].comp;
+      J.add = spec[a].add;
+      J.flag_inv = spec[a].flag_inverted;
       J.shift = 8 * passes[a][step];
-      job_array[nj] = a;
-      cur[a] = dst;
+      cur_k[a] = J.out_keys;
+      cur_v[a] = J.out_vals;
       ++nj;
     }
     dim3 grid(tiles, nj);
-    k_onesweep<<<grid, kSwBlock, 0, st>>>(jobs, n, d_err);
+    if (kv) k_onesweep<true><<<grid, kSwBlock, sweep_smem(true), st>>>(jobs, n, d_err);
+    else k_onesweep<false><<<grid, kSwBlock, sweep_smem(false), st>>>(jobs, n, d_err);
     BITS_LAUNCH_CHECK("k_onesweep");
-    (void)job_array;
   }
   return BITS_OK;
+}
+
+bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, uint32_t* out_e,
+                                 uint32_t* d_err, RadixScratch& ws, cudaStream_t st) {
+  SortSpec spec[2]{};
+  spec[0].comp = 0;
+  spec[0].out_keys = out_s;
+  spec[0].tmp_keys = ws.tmp_s;
+  spec[1].comp = 1;
+  spec[1].out_keys = out_e;
+  spec[1].tmp_keys = ws.tmp_e;
+  return radix_sort_pairs(d_b, n, spec, 0, d_err, ws, st, nullptr);
 }
 
 }  // namespace bits

@@ -7,19 +7,41 @@ namespace bits {
 
 // Device scratch one sort needs; every buffer is owned by the caller.
 struct RadixScratch {
-  uint32_t* tmp_s;    // n keys (ping-pong buffer of the start sort)
-  uint32_t* tmp_e;    // n keys (ping-pong buffer of the end sort)
-  uint32_t* hist;     // 2 arrays x 4 passes x 256 digit counters
+  uint32_t* tmp_s;    // n keys (ping-pong buffer of the first array)
+  uint32_t* tmp_e;    // n keys (ping-pong buffer of the second array)
+  uint32_t* hist;     // kRadixHistWords: 2 arrays x 4 passes x 256 digit counters + 1 flag
   uint32_t* status;   // radix_status_words(n) x 2 arrays x 4 passes look-back words
   uint32_t* tickets;  // 2 arrays x 4 passes tile tickets
+};
+
+constexpr size_t kRadixHistWords = 2 * 4 * 256 + 64;
+
+// One of the two arrays a sort produces.  Its keys come from the interval
+// pairs: word `comp` (0 start, 1 end) plus `add`.  With out_vals set, the
+// values are the intervals' indices, top bit set for inverted intervals when
+// flag_inverted is set.
+struct SortSpec {
+  int comp = 0;
+  uint32_t add = 0;
+  int flag_inverted = 0;
+  uint32_t* out_keys = nullptr;
+  uint32_t* out_vals = nullptr;  // NULL: keys only (must agree for both specs)
+  uint32_t* tmp_keys = nullptr;
+  uint32_t* tmp_vals = nullptr;
 };
 
 // Look-back words one array needs for one pass.
 size_t radix_status_words(uint32_t n);
 
-// Sort the start words and the end words of n intervals (array of (start,
-// end) pairs) into out_s / out_e.  Validates start < end (DEV_ERR_INVALID
-// into d_err, returned as BITS_EINVAL); synchronises `st` once.
+// Sort the two keys of n intervals into spec[0] and spec[1].  validate = 0:
+// every interval must have start < end (else BITS_EINVAL); validate = 1:
+// intervals with end < start are reported through *any_inverted.  Reads the
+// histograms on the host (synchronises `st` once).
+bits_status radix_sort_pairs(const uint2* d_src, uint32_t n, const SortSpec spec[2], int validate,
+                             uint32_t* d_err, RadixScratch& ws, cudaStream_t st,
+                             bool* any_inverted);
+
+// The database sort: starts into out_s, ends into out_e (keys only).
 bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, uint32_t* out_e,
                                  uint32_t* d_err, RadixScratch& ws, cudaStream_t st);
 
