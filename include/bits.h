@@ -62,7 +62,7 @@ typedef struct bits_opts {
   int32_t method;          /* bits_method the database uses by default           */
   int32_t rmi_leaves_log2; /* 0: no learned index; else 2^k linear leaves per     */
                            /* sorted array, k in [1, 22]                          */
-  int32_t top_tree_log2;   /* 0: default 13; the top level of each array's        */
+  int32_t top_tree_log2;   /* 0: default 12; the top level of each array's        */
                            /* 16-ary search tree kept in shared memory holds at   */
                            /* most 2^k - 1 keys, k in [2, 14]                     */
   int32_t reserved;        /* must be 0                                           */
@@ -158,6 +158,17 @@ bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
 #define BITS_NOALLOC_MAX_INTERVALS 262144u
 bits_status bits_sort_intervals_noalloc(const uint32_t* d_b, uint64_t n, uint32_t* d_bs,
                                         uint32_t* d_be, void* stream);
+
+/*
+ * bits_selftest_wait -- diagnostic of the bounded device-side waits (not in
+ * the paper).  Every spin-wait of the library (the radix sort's look-back)
+ * gives up after a fixed number of iterations, records a timeout and
+ * returns, so a lost peer cannot hang the GPU.  This call runs the same kind
+ * of wait on a device word that nothing sets, with spin_limit iterations
+ * (1 .. 2^23, each sleeping about 64 ns): it returns BITS_ETIMEOUT, and the
+ * context stays usable.  Synchronises `stream`.
+ */
+bits_status bits_selftest_wait(uint32_t spin_limit, void* stream);
 
 /* Read-only views of the database (sorted starts, sorted ends, size). */
 bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_t** d_be,

@@ -94,7 +94,7 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   }
   bits_opts o{};
   if (opts) o = *opts;
-  const int t = o.top_tree_log2 ? o.top_tree_log2 : 13;
+  const int t = o.top_tree_log2 ? o.top_tree_log2 : 12;
   if (t < 2 || t > 14 || o.rmi_leaves_log2 < 0 || o.rmi_leaves_log2 > 22 || o.reserved != 0 ||
       o.method < 0 || o.method > BITS_METHOD_MERGEPATH) {
     set_error("bits_build_db: option out of range");

@@ -123,10 +123,10 @@ k_mc_search(McArgs P, LevelIndex L, RmiView R) {
       uint32_t rs, re;
       const uint32_t key_s = end, key_e = start + 1u;
       if (kRmi) {
-        rmi_rank2(R, L, P.nb, key_s, key_e, rs, re);
+        rmi_rank2(R, L, P.nb, key_s, key_e, rs, re, false);
       } else {
         top_rank2(s_top, L.top_size, key_s, key_e, rs, re);
-        quad_descend(L, rs, key_s, re, key_e);
+        quad_descend(L, rs, key_s, re, key_e, false);
       }
       acc += icount_from_ranks(rs, re, start, P.nb);
     }

@@ -114,7 +114,7 @@ __device__ __forceinline__ uint32_t rmi_finish(const uint32_t* __restrict__ X, u
 // must call it).  On return rs = #(B_S < key_s), re = #(B_E < key_e).
 __device__ __forceinline__ void rmi_rank2(const RmiView& R, const LevelIndex& L, uint32_t nb,
                                           uint32_t key_s, uint32_t key_e, uint32_t& rs,
-                                          uint32_t& re) {
+                                          uint32_t& re, bool stream_level0 = true) {
   uint32_t wls, whs, wle, whe;
   rmi_window(R, 0, key_s, nb, wls, whs);
   rmi_window(R, 1, key_e, nb, wle, whe);
@@ -123,7 +123,7 @@ __device__ __forceinline__ void rmi_rank2(const RmiView& R, const LevelIndex& L,
   const int ds = js <= L.J ? js : 0, de = je <= L.J ? je : 0;
   uint32_t is = ds ? wls >> (4 * ds) : 0u, ie = de ? wle >> (4 * de) : 0u;
   const int jmax = __reduce_max_sync(0xFFFFFFFFu, max(ds, de));
-  if (jmax > 0) quad_descend_from(L, jmax, ds, is, key_s, de, ie, key_e);
+  if (jmax > 0) quad_descend_from(L, jmax, ds, is, key_s, de, ie, key_e, stream_level0);
   rs = rmi_finish(L.lv[0][0], nb, key_s, js, L.J, is, wls, whs);
   re = rmi_finish(L.lv[1][0], nb, key_e, je, L.J, ie, wle, whe);
 }

@@ -38,6 +38,30 @@ __device__ __forceinline__ uint4 ldg4(const uint32_t* p) {
   return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
+// L2 cache policies for the tree levels.  The upper levels (1/16, 1/256, ...
+// of the array) are re-read by every search and should stay in L2; the
+// level-0 chunks are touched about once per search and should not push them
+// out.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// 16-byte read-only load with an L2 cache policy.
+__device__ __forceinline__ uint4 ldg4_hint(const uint32_t* p, uint64_t policy) {
+  uint4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(policy));
+  return v;
+}
+
 __device__ __forceinline__ uint32_t cnt4(const uint4 v, uint32_t key) {
   return (uint32_t)(v.x < key) + (uint32_t)(v.y < key) + (uint32_t)(v.z < key) +
          (uint32_t)(v.w < key);
@@ -74,8 +98,11 @@ __device__ __forceinline__ void load_top(uint32_t* s_top, const LevelIndex& L) {
 // lanes pass js = je = 0).
 __device__ __forceinline__ void quad_descend_from(const LevelIndex& L, int jmax, int js,
                                                   uint32_t& is_out, uint32_t key_s, int je,
-                                                  uint32_t& ie_out, uint32_t key_e) {
+                                                  uint32_t& ie_out, uint32_t key_e,
+                                                  bool stream_level0 = true) {
   const unsigned lane = lane_id(), sub = lane & 3u, qbase = lane & ~3u;
+  const uint64_t pol_last = policy_evict_last();
+  const uint64_t pol_first = stream_level0 ? policy_evict_first() : pol_last;
   uint32_t is[4], ks[4], ie[4], ke[4];
   int jss[4], jes[4];
   #pragma unroll
@@ -93,12 +120,13 @@ __device__ __forceinline__ void quad_descend_from(const LevelIndex& L, int jmax,
     const uint32_t lenj = L.len[j], lenm = L.len[j - 1];
     const uint32_t* LS = L.lv[0][j - 1];
     const uint32_t* LE = L.lv[1][j - 1];
+    const uint64_t pol = j == 1 ? pol_first : pol_last;
     uint4 vs[4], ve[4];
     #pragma unroll
     for (int o = 0; o < 4; ++o) {
-      vs[o] = (j <= jss[o] && is[o] < lenj) ? ldg4(LS + 16u * is[o] + 4u * sub)
+      vs[o] = (j <= jss[o] && is[o] < lenj) ? ldg4_hint(LS + 16u * is[o] + 4u * sub, pol)
                                             : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
-      ve[o] = (j <= jes[o] && ie[o] < lenj) ? ldg4(LE + 16u * ie[o] + 4u * sub)
+      ve[o] = (j <= jes[o] && ie[o] < lenj) ? ldg4_hint(LE + 16u * ie[o] + 4u * sub, pol)
                                             : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
     }
     #pragma unroll
@@ -117,9 +145,14 @@ __device__ __forceinline__ void quad_descend_from(const LevelIndex& L, int jmax,
 }
 
 // Plain descent: both searches of every thread enter at the top level J.
+// stream_level0: the level-0 chunks are read about once (database larger
+// than L2); false when the whole database is meant to stay in L2.
 __device__ __forceinline__ void quad_descend(const LevelIndex& L, uint32_t& is_out,
-                                             uint32_t key_s, uint32_t& ie_out, uint32_t key_e) {
+                                             uint32_t key_s, uint32_t& ie_out, uint32_t key_e,
+                                             bool stream_level0 = true) {
   const unsigned lane = lane_id(), sub = lane & 3u, qbase = lane & ~3u;
+  const uint64_t pol_last = policy_evict_last();
+  const uint64_t pol_first = stream_level0 ? policy_evict_first() : pol_last;
   uint32_t is[4], ks[4], ie[4], ke[4];
   #pragma unroll
   for (int o = 0; o < 4; ++o) {
@@ -134,12 +167,13 @@ __device__ __forceinline__ void quad_descend(const LevelIndex& L, uint32_t& is_o
     const uint32_t lenj = L.len[j], lenm = L.len[j - 1];
     const uint32_t* LS = L.lv[0][j - 1];
     const uint32_t* LE = L.lv[1][j - 1];
+    const uint64_t pol = j == 1 ? pol_first : pol_last;
     uint4 vs[4], ve[4];
     #pragma unroll
     for (int o = 0; o < 4; ++o) {
-      vs[o] = is[o] < lenj ? ldg4(LS + 16u * is[o] + 4u * sub)
+      vs[o] = is[o] < lenj ? ldg4_hint(LS + 16u * is[o] + 4u * sub, pol)
                            : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
-      ve[o] = ie[o] < lenj ? ldg4(LE + 16u * ie[o] + 4u * sub)
+      ve[o] = ie[o] < lenj ? ldg4_hint(LE + 16u * ie[o] + 4u * sub, pol)
                            : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
     }
     #pragma unroll
