@@ -182,7 +182,7 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
       hd[j].nb = dbs[j]->n;
       hd[j].method = m;
       hd[j].err = dbs[j]->err;
-      if (m != BITS_METHOD_RMI) max_top = std::max<size_t>(max_top, dbs[j]->lvl.top_size);
+      if (m != BITS_METHOD_RMI) max_top = std::max<size_t>(max_top, top_words(dbs[j]->lvl.top_size));
     }
     cudaFreeAsync(d_tmp, st);
     // Units: largest database first, then set by set, kChunk queries each.

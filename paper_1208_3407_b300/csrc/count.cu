@@ -153,7 +153,7 @@ bits_status launch_count_search(const bits_db* db, const uint32_t* d_a, uint32_t
                                 uint32_t* d_counts, uint64_t* d_total, cudaStream_t st) {
   BITS_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), st));
   if (n == 0) return BITS_OK;
-  const size_t smem = sizeof(uint32_t) * 2 * db->lvl.top_size;
+  const size_t smem = sizeof(uint32_t) * 2 * top_words(db->lvl.top_size);
   const uint32_t need = (n + kCountBlock - 1) / kCountBlock;
   const uint32_t grid = std::min<uint32_t>(need, (uint32_t)(count_blocks_per_sm(smem) * sm_count()));
   k_count_search<<<grid, kCountBlock, smem, st>>>(reinterpret_cast<const uint2*>(d_a), n, db->lvl,

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kMcBlock)
 k_mc_search(McArgs P, LevelIndex L, RmiView R) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* s_top = smem;
-  uint32_t* s_off = s_top + (kRmi ? 0u : 2u * L.top_size);
+  uint32_t* s_off = s_top + (kRmi ? 0u : 2u * top_words(L.top_size));
   uint32_t* s_rng = s_off + kMcChunk;
   uint32_t* s_len = s_rng + kMcChunk;
   uint32_t* s_coff = s_len + kMcChunk;
@@ -146,7 +146,7 @@ __global__ void k_mc_tally(const unsigned long long* __restrict__ totals, uint32
 }
 
 size_t mc_smem_bytes(const LevelIndex& L, uint32_t nc, bool rmi) {
-  return sizeof(uint32_t) * ((rmi ? 0 : 2 * L.top_size) + 3 * kMcChunk + 2 * nc);
+  return sizeof(uint32_t) * ((rmi ? 0 : 2 * top_words(L.top_size)) + 3 * kMcChunk + 2 * nc);
 }
 
 template <bool kRmi>

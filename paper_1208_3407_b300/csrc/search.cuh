@@ -67,26 +67,43 @@ __device__ __forceinline__ uint32_t cnt4(const uint4 v, uint32_t key) {
          (uint32_t)(v.w < key);
 }
 
+// Shared-memory layout of the top level.  A power-of-two search probes index
+// pos + step - 1, which for step >= 32 is the same index mod 32 in every
+// lane: all 32 lanes would hit one bank.  One pad word after every 32
+// entries sends those probes to different banks.
+__device__ __forceinline__ uint32_t top_slot(uint32_t i) { return i + (i >> 5); }
+__host__ __device__ __forceinline__ uint32_t top_words(uint32_t size) { return size + (size >> 5); }
+
 // #(s[0 .. size-1) < key) for a power-of-two size whose tail is padded with
-// 0xFFFFFFFF; two independent searches in lock step.
+// 0xFFFFFFFF; two independent searches in lock step.  s_top holds the start
+// array then the end array, each in the padded layout of top_slot.
 __device__ __forceinline__ void top_rank2(const uint32_t* __restrict__ s_top, uint32_t size,
                                           uint32_t key_s, uint32_t key_e, uint32_t& is,
                                           uint32_t& ie) {
-  const uint32_t* s_e = s_top + size;
+  const uint32_t* s_e = s_top + top_words(size);
   uint32_t ps = 0u, pe = 0u;
   for (uint32_t step = size >> 1; step; step >>= 1) {
-    if (s_top[ps + step - 1u] < key_s) ps += step;
-    if (s_e[pe + step - 1u] < key_e) pe += step;
+    if (s_top[top_slot(ps + step - 1u)] < key_s) ps += step;
+    if (s_e[top_slot(pe + step - 1u)] < key_e) pe += step;
   }
   is = ps;
   ie = pe;
 }
 
-// Cooperative copy of the two top-level images into shared memory.
+// Cooperative copy of the two top-level images into shared memory, padded.
 __device__ __forceinline__ void load_top(uint32_t* s_top, const LevelIndex& L) {
   const uint4* src = reinterpret_cast<const uint4*>(L.top);
-  uint4* dst = reinterpret_cast<uint4*>(s_top);
-  for (uint32_t i = threadIdx.x; i < (2u * L.top_size) / 4u; i += blockDim.x) dst[i] = src[i];
+  const uint32_t size = L.top_size, words = top_words(size);
+  for (uint32_t i = threadIdx.x; i < (2u * size) / 4u; i += blockDim.x) {
+    const uint4 v = src[i];
+    const uint32_t e = 4u * i;                       // element index over both arrays
+    const uint32_t a = e >= size ? 1u : 0u;          // which array
+    uint32_t* dst = s_top + a * words + top_slot(e - a * size);  // 4 | 32, so one pad run
+    dst[0] = v.x;
+    dst[1] = v.y;
+    dst[2] = v.z;
+    dst[3] = v.w;
+  }
 }
 
 // Descend the 16-ary levels for the two searches (starts, ends) of every
