@@ -360,13 +360,20 @@ def run_ours(args):
     t4 = torch.empty(1, dtype=torch.uint64, device=dev)
     scale_forms = {}
     steps4 = max(3, min(args.steps, 5))
-    for name, m in (("search", bits.METHOD_SEARCH), ("rmi", bits.METHOD_RMI)):
-        ms, _, _ = timed(lambda m=m: db4.count(a4, counts=c4, total=t4, method=m, check=False),
-                         steps4, 3)
+    totals4 = {}
+    for name, m, per_query in (("search", bits.METHOD_SEARCH, True),
+                               ("rmi", bits.METHOD_RMI, True),
+                               ("mergepath", bits.METHOD_MERGEPATH, True),
+                               ("search_total_only", bits.METHOD_SEARCH, False),
+                               ("mergepath_total_only", bits.METHOD_MERGEPATH, False)):
+        out_c = c4 if per_query else False
+        ms, _, _ = timed(lambda m=m, out_c=out_c: db4.count(a4, counts=out_c, total=t4, method=m,
+                                                            check=False), steps4, 3)
+        totals4[name] = int(t4.cpu().numpy()[0])
         scale_forms[name] = {"ms_per_step": ms,
-                             "queries_per_s": world * a4_np.shape[0] / (ms * 1e-3),
-                             "hbm_gbs_at_76B_per_query": 76.0 * a4_np.shape[0] / (ms * 1e-3) / 1e9}
+                             "queries_per_s": world * a4_np.shape[0] / (ms * 1e-3)}
     db4.check()
+    assert len(set(totals4.values())) == 1, totals4
     idx4 = np.random.default_rng(2).choice(a4_np.shape[0], size=16, replace=False)
     oc4, _ = o.count_brute(a4_np[idx4], b4_np)
     scale = {"workload": "100,000,000 uniform queries vs 100,000,000 intervals from 1000 "
