@@ -50,7 +50,11 @@ def _declare(lib):
     lib.or_mc.argtypes = [u32p, C.c_uint64, u32p, u32p, C.c_uint32, u32p, u32p, C.c_uint64,
                           C.c_uint64, C.c_uint32, C.c_uint32, u64p, u64p, u64p,
                           C.POINTER(C.c_double), C.c_int]
-    for f in ("or_count_brute", "or_build", "or_count_sorted", "or_mc_place", "or_mc"):
+    lib.or_count_brute_closed.argtypes = [u32p, C.c_uint64, u32p, C.c_uint64, u32p, u64p]
+    lib.or_project.argtypes = [u32p, u32p, u32p, C.c_uint64, u32p, u32p, C.c_uint32, C.c_int, u32p]
+    lib.or_project.restype = C.c_uint64
+    for f in ("or_count_brute", "or_build", "or_count_sorted", "or_mc_place", "or_mc",
+              "or_count_brute_closed"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -96,6 +100,32 @@ class Oracle:
         if self.lib.or_count_brute(_p32(a), a.shape[0], _p32(b), b.shape[0], _p32(counts), _p64(total)):
             raise ValueError("oracle rejected input")
         return counts, int(total[0])
+
+    def count_brute_closed(self, a, b):
+        """Sec. 1.1's closed predicate, by brute force (intervals [start, end])."""
+        a, b = _iv(a), _iv(b)
+        counts = np.zeros(a.shape[0], np.uint32)
+        total = np.zeros(1, np.uint64)
+        if self.lib.or_count_brute_closed(_p32(a), a.shape[0], _p32(b), b.shape[0], _p32(counts),
+                                          _p64(total)):
+            raise ValueError("oracle rejected input")
+        return counts, int(total[0])
+
+    def project(self, chrom, start, end, contig_off=None, contig_len=None, closed=False):
+        """Sec. 2.3 projection; returns (intervals, number rejected).  Rejected rows
+        are (2^32 - 1, 0).  With no contig table the line is one contig at 0."""
+        start = np.ascontiguousarray(start, np.uint32)
+        end = np.ascontiguousarray(end, np.uint32)
+        n = start.shape[0]
+        chrom = np.ascontiguousarray(np.zeros(n) if chrom is None else chrom, np.uint32)
+        co = np.ascontiguousarray([] if contig_off is None else contig_off, np.uint32)
+        cl = np.ascontiguousarray([] if contig_len is None else contig_len, np.uint32)
+        out = np.zeros((n, 2), np.uint32)
+        nil = C.cast(0, C.POINTER(C.c_uint32))
+        bad = self.lib.or_project(_p32(chrom), _p32(start), _p32(end), n,
+                                  _p32(co) if co.size else nil, _p32(cl) if cl.size else nil,
+                                  co.shape[0], 1 if closed else 0, _p32(out))
+        return out, int(bad)
 
     def build(self, b):
         b = _iv(b)

@@ -264,4 +264,72 @@ int or_mc(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* 
   return 0;
 }
 
+// Sec. 1.1's predicate exactly as printed, for closed intervals [start, end]:
+// a and b intersect iff a.start <= b.end and a.end >= b.start.  Brute force.
+int or_count_brute_closed(const uint32_t* a, uint64_t na, const uint32_t* b, uint64_t nb,
+                          uint32_t* counts, uint64_t* total) {
+  for (uint64_t j = 0; j < nb; ++j)
+    if (b[2 * j + 1] < b[2 * j]) return 1;
+  if (check_queries(a, na)) return 1;
+  uint64_t t = 0;
+  for (uint64_t i = 0; i < na; ++i) {
+    uint32_t c = 0;
+    for (uint64_t j = 0; j < nb; ++j)
+#ifdef ORACLE_MUTANT_BRUTE_CLOSED
+      c += (a[2 * i] < b[2 * j + 1] && a[2 * i + 1] > b[2 * j]) ? 1u : 0u;
+#else
+      c += (a[2 * i] <= b[2 * j + 1] && a[2 * i + 1] >= b[2 * j]) ? 1u : 0u;
+#endif
+    if (counts) counts[i] = c;
+    t += c;
+  }
+  *total = t;
+  return 0;
+}
+
+// Projection of chromosome-local intervals onto one line (Sec. 2.3): interval
+// i on contig chrom[i] becomes [off[chrom] + start, off[chrom] + end), with one
+// added to the end for closed input, since [s, e] on the integers is
+// [s, e + 1).  With no contig table (nc == 0) every interval is on one
+// contig at offset 0 that spans the whole 32-bit line.  An interval that
+// cannot be projected (contig id out of range, start > end, end past its
+// contig, or an end that does not fit in 32 bits) is written as the inverted
+// pair (2^32 - 1, 0), which every counting call rejects; the return value is
+// the number of such intervals.
+uint64_t or_project(const uint32_t* chrom, const uint32_t* start, const uint32_t* end, uint64_t n,
+                    const uint32_t* coff, const uint32_t* clen, uint32_t nc, int closed,
+                    uint32_t* out) {
+  uint64_t bad = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    uint64_t off = 0, len = 0xFFFFFFFFull;
+    bool ok = true;
+    if (nc) {
+      const uint32_t c = chrom[i];
+      ok = c < nc;
+      if (ok) {
+        off = coff[c];
+        len = clen[c];
+      }
+    }
+#ifdef ORACLE_MUTANT_PROJECT_CLOSED
+    const uint64_t e = uint64_t(end[i]);
+#else
+    const uint64_t e = uint64_t(end[i]) + (closed ? 1u : 0u);
+#endif
+#ifdef ORACLE_MUTANT_PROJECT_OFFSET
+    if (nc && ok) off = coff[0];
+#endif
+    ok = ok && start[i] <= end[i] && e <= len && off + e <= 0xFFFFFFFFull;
+    if (ok) {
+      out[2 * i] = uint32_t(off + start[i]);
+      out[2 * i + 1] = uint32_t(off + e);
+    } else {
+      out[2 * i] = 0xFFFFFFFFu;
+      out[2 * i + 1] = 0u;
+      ++bad;
+    }
+  }
+  return bad;
+}
+
 }  // extern "C"

@@ -34,3 +34,29 @@ def read_philox_kat():
                 w = [int(x, 16) for x in line]
                 rows.append((w[0:4], w[4:6], w[6:10]))
     return rows
+
+
+def read_projection_fixture():
+    """Returns (contig_off, contig_len, chrom, start, end, half_open, closed); the last two
+    are lists of (start, end) or None for a rejected row."""
+    table, rows = {}, []
+    with open(os.path.join(GOLDEN, "projection.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if not line:
+                continue
+            if line[0] == "C":
+                table[int(line[1])] = (int(line[2]), int(line[3]))
+            elif line[0] == "P":
+                v = line[1:]
+                ho = None if v[3] == "x" else (int(v[3]), int(v[4]))
+                cl = None if v[5] == "x" else (int(v[5]), int(v[6]))
+                rows.append((int(v[0]), int(v[1]), int(v[2]), ho, cl))
+    ids = sorted(table)
+    assert ids == list(range(len(ids)))
+    co = np.array([table[i][0] for i in ids], np.uint32)
+    cl_ = np.array([table[i][1] for i in ids], np.uint32)
+    chrom = np.array([r[0] for r in rows], np.uint32)
+    start = np.array([r[1] for r in rows], np.uint32)
+    end = np.array([r[2] for r in rows], np.uint32)
+    return co, cl_, chrom, start, end, [r[3] for r in rows], [r[4] for r in rows]

@@ -14,7 +14,7 @@ import pytest
 
 import bits_synth as synth
 import oracle
-from goldens import read_count_fixture, read_philox_kat
+from goldens import read_count_fixture, read_philox_kat, read_projection_fixture
 
 O = oracle.get()
 
@@ -243,10 +243,99 @@ def test_mc_tally_and_pvalue():
     assert (tz == 0).all() and oz == 0 and kz == 9 and pz == 1.0
 
 
+# ------------------------------------------------ projection and closed intervals (Sec. 1.1, 2.3)
+
+def _expected_rows(rows):
+    return np.array([r if r is not None else (0xFFFFFFFF, 0) for r in rows], np.uint32), \
+        sum(r is None for r in rows)
+
+
+@pytest.mark.parametrize("closed", [False, True])
+def test_projection_golden(closed):
+    co, cl, chrom, s, e, ho, cc = read_projection_fixture()
+    out, bad = O.project(chrom, s, e, co, cl, closed=closed)
+    exp, nbad = _expected_rows(cc if closed else ho)
+    np.testing.assert_array_equal(out, exp)
+    assert bad == nbad
+
+
+def test_closed_predicate_golden():
+    # The printed predicate, brute force, against hand counts; then the same
+    # sets mapped to half-open [s, e + 1) and counted by both half-open forms.
+    a, b, exp, total = read_count_fixture("closed.txt")
+    c, t = O.count_brute_closed(a, b)
+    np.testing.assert_array_equal(c, exp)
+    assert t == total
+    pa, bad_a = O.project(None, a[:, 0], a[:, 1], closed=True)
+    pb, bad_b = O.project(None, b[:, 0], b[:, 1], closed=True)
+    assert bad_a == 0 and bad_b == 0
+    for fn in (O.count_brute, O.count):
+        c2, t2 = fn(pa, pb)
+        np.testing.assert_array_equal(c2, exp)
+        assert t2 == total
+
+
+def _local_sets(rng, n, lens):
+    chrom = rng.integers(0, len(lens), size=n)
+    ln = 1 + (rng.random(n) * np.minimum(11, lens[chrom])).astype(np.int64)
+    s = (rng.random(n) * (lens[chrom] - ln + 1)).astype(np.int64)
+    return chrom, s, s + ln
+
+
+@pytest.mark.parametrize("closed", [False, True])
+def test_projection_matches_per_contig_brute_force(closed):
+    # Intervals on different chromosomes never meet, and on the same one they
+    # meet by the local predicate: counted here pair by pair on the local
+    # coordinates, with no projection, and compared with counting the
+    # projected sets on one line.
+    rng = np.random.default_rng(5)
+    lens = np.array([40, 7, 90, 25, 60], np.int64)
+    off = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    ca, sa, ea = _local_sets(rng, 300, lens)
+    cb, sb, eb = _local_sets(rng, 400, lens)
+    if closed:                      # closed [s, e] with e = s + len - 1
+        ea, eb = ea - 1, eb - 1
+    same = ca[:, None] == cb[None, :]
+    if closed:
+        meet = (sa[:, None] <= eb[None, :]) & (ea[:, None] >= sb[None, :])
+    else:
+        meet = (sb[None, :] < ea[:, None]) & (eb[None, :] > sa[:, None])
+    expect = (same & meet).sum(1)
+    pa, bad_a = O.project(ca, sa, ea, off, lens, closed=closed)
+    pb, bad_b = O.project(cb, sb, eb, off, lens, closed=closed)
+    assert bad_a == 0 and bad_b == 0
+    c, t = O.count(pa, pb)
+    np.testing.assert_array_equal(c, expect)
+    assert t == int(expect.sum())
+    # Projected intervals stay inside their chromosome and keep their length.
+    ln = (ea - sa) + (1 if closed else 0)
+    assert (pa[:, 0] >= off[ca]).all() and (pa[:, 1] <= off[ca] + lens[ca]).all()
+    np.testing.assert_array_equal(pa[:, 1].astype(np.int64) - pa[:, 0], ln)
+
+
+def test_projection_rejects_and_edges():
+    # No contig table: one line at offset 0 spanning 32 bits.
+    top = 0xFFFFFFFF
+    out, bad = O.project(None, [0, 0, 5, top], [top, top, 4, top], closed=False)
+    np.testing.assert_array_equal(out, [[0, top], [0, top], [top, 0], [top, top]])
+    assert bad == 1
+    out, bad = O.project(None, [0, top - 1], [top, top - 1], closed=True)
+    np.testing.assert_array_equal(out, [[top, 0], [top - 1, top]])
+    assert bad == 1
+    # A chromosome whose end reaches 2^32 - 1 exactly is usable; one past is not.
+    out, bad = O.project([0, 0], [0, 0], [10, 11], [top - 10], [11], closed=False)
+    np.testing.assert_array_equal(out, [[top - 10, top], [top, 0]])
+    assert bad == 1
+    out, bad = O.project([], [], [], [0], [5])
+    assert out.shape == (0, 2) and bad == 0
+
+
 # ------------------------------------------------------------------- planted mistakes
 
 MUTANTS = ["ORACLE_MUTANT_CLOSED", "ORACLE_MUTANT_LAST_LOWER", "ORACLE_MUTANT_PHILOX",
-           "ORACLE_MUTANT_SCALE", "ORACLE_MUTANT_WORD_ORDER", "ORACLE_MUTANT_TALLY"]
+           "ORACLE_MUTANT_SCALE", "ORACLE_MUTANT_WORD_ORDER", "ORACLE_MUTANT_TALLY",
+           "ORACLE_MUTANT_PROJECT_OFFSET", "ORACLE_MUTANT_PROJECT_CLOSED",
+           "ORACLE_MUTANT_BRUTE_CLOSED"]
 
 
 def _pins_pass(o: oracle.Oracle) -> bool:
@@ -271,6 +360,14 @@ def _pins_pass(o: oracle.Oracle) -> bool:
         bs, be = o.build(bb)
         tot, obs, k, p = o.mc(aa, co, cl, bs, be, seed=1, s_begin=0, s_end=4)
         assert k == 4 and p == 1.0
+        co, cl, chrom, s, e, ho, cc = read_projection_fixture()
+        for closed, rows in ((False, ho), (True, cc)):
+            out, bad = o.project(chrom, s, e, co, cl, closed=closed)
+            exp, nbad = _expected_rows(rows)
+            assert (out == exp).all() and bad == nbad
+        a, b, exp, total = read_count_fixture("closed.txt")
+        c, t = o.count_brute_closed(a, b)
+        assert (c == exp).all() and t == total
         return True
     except AssertionError:
         return False
