@@ -50,11 +50,17 @@ def _declare(lib):
     lib.or_mc.argtypes = [u32p, C.c_uint64, u32p, u32p, C.c_uint32, u32p, u32p, C.c_uint64,
                           C.c_uint64, C.c_uint32, C.c_uint32, u64p, u64p, u64p,
                           C.POINTER(C.c_double), C.c_int]
+    lib.or_mc_place_set.argtypes = [u32p, C.c_uint64, u32p, u32p, C.c_uint32, C.c_uint64, C.c_uint32,
+                                    C.c_uint32, u32p]
+    lib.or_mc_set.argtypes = [u32p, C.c_uint64, u32p, u32p, C.c_uint32, u32p, u32p, C.c_uint64,
+                              C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, u64p, u64p, u64p,
+                              C.POINTER(C.c_double), C.c_int]
+    lib.or_mc_summary.argtypes = [u64p, C.c_uint64, C.c_uint64, u64p, C.POINTER(C.c_double)]
     lib.or_count_brute_closed.argtypes = [u32p, C.c_uint64, u32p, C.c_uint64, u32p, u64p]
     lib.or_project.argtypes = [u32p, u32p, u32p, C.c_uint64, u32p, u32p, C.c_uint32, C.c_int, u32p]
     lib.or_project.restype = C.c_uint64
     for f in ("or_count_brute", "or_build", "or_count_sorted", "or_mc_place", "or_mc",
-              "or_count_brute_closed"):
+              "or_count_brute_closed", "or_mc_place_set", "or_mc_set", "or_mc_summary"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -161,17 +167,18 @@ class Oracle:
     def scale_u64(self, u: int, n: int) -> int:
         return int(self.lib.or_scale_u64(u, n))
 
-    def mc_place(self, a, contig_off, contig_len, seed: int, s: int):
+    def mc_place(self, a, contig_off, contig_len, seed: int, s: int, set_index: int = 0):
         a = _iv(a)
         co = np.ascontiguousarray(contig_off, np.uint32)
         cl = np.ascontiguousarray(contig_len, np.uint32)
         out = np.zeros_like(a)
-        if self.lib.or_mc_place(_p32(a), a.shape[0], _p32(co), _p32(cl), co.shape[0], seed, s, _p32(out)):
+        if self.lib.or_mc_place_set(_p32(a), a.shape[0], _p32(co), _p32(cl), co.shape[0], seed, s,
+                                    set_index, _p32(out)):
             raise ValueError("oracle rejected MC input")
         return out
 
     def mc(self, a, contig_off, contig_len, bs, be, seed: int, s_begin: int, s_end: int,
-           threads: int = 1):
+           threads: int = 1, set_index: int = 0):
         a = _iv(a)
         co = np.ascontiguousarray(contig_off, np.uint32)
         cl = np.ascontiguousarray(contig_len, np.uint32)
@@ -182,11 +189,23 @@ class Oracle:
         k = np.zeros(1, np.uint64)
         p = C.c_double(0.0)
         tp = _p64(totals) if totals.size else C.cast(0, C.POINTER(C.c_uint64))
-        if self.lib.or_mc(_p32(a), a.shape[0], _p32(co), _p32(cl), co.shape[0], _p32(bs), _p32(be),
-                          bs.shape[0], seed, s_begin, s_end, tp, _p64(obs), _p64(k), C.byref(p),
-                          threads):
+        if self.lib.or_mc_set(_p32(a), a.shape[0], _p32(co), _p32(cl), co.shape[0], _p32(bs),
+                              _p32(be), bs.shape[0], seed, s_begin, s_end, set_index, tp,
+                              _p64(obs), _p64(k), C.byref(p), threads):
             raise ValueError("oracle rejected MC input")
         return totals, int(obs[0]), int(k[0]), p.value
+
+    def mc_summary(self, totals, observed: int) -> dict:
+        """Tally, middles and enrichment score of one MC test (Sec. 3.2, Fig. 3)."""
+        t = np.ascontiguousarray(totals, np.uint64)
+        ints = np.zeros(5, np.uint64)
+        dbl = (C.c_double * 3)()
+        tp = _p64(t) if t.size else C.cast(0, C.POINTER(C.c_uint64))
+        if self.lib.or_mc_summary(tp, t.shape[0], observed, _p64(ints), dbl):
+            raise ValueError("oracle: 64-bit overflow in the summary")
+        return {"observed": int(ints[0]), "k_ge": int(ints[1]), "k_le": int(ints[2]),
+                "median_lo": int(ints[3]), "median_hi": int(ints[4]), "p_enrich": dbl[0],
+                "p_deplete": dbl[1], "log2_enrichment": dbl[2]}
 
 
 _default: Oracle | None = None

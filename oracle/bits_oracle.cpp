@@ -27,6 +27,7 @@
 // Build: g++ -O2 -std=c++17 -shared -fPIC -pthread bits_oracle.cpp -o liboracle.so
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <thread>
@@ -196,9 +197,12 @@ uint64_t or_scale_u64(uint64_t u, uint64_t n) { return scale_u64(u, n); }
 
 // New placement of every A interval for shuffle s (Sec. 3.2 null model).
 // out receives [start, end) pairs.  Returns 1 if an interval is inverted,
-// lies outside every contig, or crosses its contig's end.
-int or_mc_place(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* clen,
-                uint32_t nc, uint64_t seed, uint32_t s, uint32_t* out) {
+// lies outside every contig, or crosses its contig's end.  `set` is the
+// index of the query set in a screen of many sets (Sec. 3.3): interval i of
+// set `set` in shuffle s draws the Philox block at counter (i, s, set, 0), so
+// every set has its own stream and a single test is set 0.
+int or_mc_place_set(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* clen,
+                    uint32_t nc, uint64_t seed, uint32_t s, uint32_t set, uint32_t* out) {
   const uint32_t key[2] = {uint32_t(seed), uint32_t(seed >> 32)};
   for (uint64_t i = 0; i < na; ++i) {
     uint32_t as = a[2 * i], ae = a[2 * i + 1];
@@ -208,7 +212,11 @@ int or_mc_place(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint
     uint64_t cend = uint64_t(coff[c]) + clen[c];
     if (uint64_t(ae) > cend) return 1;
     uint32_t len = ae - as;
-    const uint32_t ctr[4] = {uint32_t(i), s, 0u, 0u};
+#ifdef ORACLE_MUTANT_SET_WORD
+    const uint32_t ctr[4] = {uint32_t(i), s, 0u, set};  // planted: set in word 3
+#else
+    const uint32_t ctr[4] = {uint32_t(i), s, set, 0u};
+#endif
     uint32_t x[4];
     philox4x32_10(ctr, key, x);
 #ifdef ORACLE_MUTANT_WORD_ORDER
@@ -227,10 +235,10 @@ int or_mc_place(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint
 // Monte-Carlo significance test (Sec. 3.2): totals[s - s_begin] for each
 // shuffle in [s_begin, s_end), the observed total of the unshuffled A, the
 // tally k_ge = #{s : T_s >= T_obs} and p = (k_ge + 1) / (N + 1).
-int or_mc(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* clen,
-          uint32_t nc, const uint32_t* bs, const uint32_t* be, uint64_t nb, uint64_t seed,
-          uint32_t s_begin, uint32_t s_end, uint64_t* totals, uint64_t* observed,
-          uint64_t* k_ge, double* pvalue, int threads) {
+int or_mc_set(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* clen,
+              uint32_t nc, const uint32_t* bs, const uint32_t* be, uint64_t nb, uint64_t seed,
+              uint32_t s_begin, uint32_t s_end, uint32_t set, uint64_t* totals,
+              uint64_t* observed, uint64_t* k_ge, double* pvalue, int threads) {
   if (s_end < s_begin) return 1;
   uint64_t obs = 0;
   if (or_count_sorted(a, na, bs, be, nb, nullptr, &obs, 1)) return 1;
@@ -241,7 +249,8 @@ int or_mc(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* 
   parallel_ranges(nsh, std::max(1, threads), [&](uint64_t lo, uint64_t hi) {
     std::vector<uint32_t> placed(2 * na);
     for (uint64_t k = lo; k < hi; ++k) {
-      if (or_mc_place(a, na, coff, clen, nc, seed, uint32_t(s_begin + k), placed.data())) {
+      if (or_mc_place_set(a, na, coff, clen, nc, seed, uint32_t(s_begin + k), set,
+                          placed.data())) {
         bad_part[per ? lo / per : 0] = 1;
         return;
       }
@@ -261,6 +270,62 @@ int or_mc(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* 
   *observed = obs;
   *k_ge = k;
   *pvalue = double(k + 1) / double(nsh + 1);
+  return 0;
+}
+
+int or_mc_place(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* clen,
+                uint32_t nc, uint64_t seed, uint32_t s, uint32_t* out) {
+  return or_mc_place_set(a, na, coff, clen, nc, seed, s, 0u, out);
+}
+
+int or_mc(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* clen,
+          uint32_t nc, const uint32_t* bs, const uint32_t* be, uint64_t nb, uint64_t seed,
+          uint32_t s_begin, uint32_t s_end, uint64_t* totals, uint64_t* observed,
+          uint64_t* k_ge, double* pvalue, int threads) {
+  return or_mc_set(a, na, coff, clen, nc, bs, be, nb, seed, s_begin, s_end, 0u, totals, observed,
+                   k_ge, pvalue, threads);
+}
+
+// Summary of one Monte-Carlo test (Sec. 3.2, Sec. 3.3 and Fig. 3):
+//   ints[0] observed total        ints[1] k_ge = #{s : T_s >= observed}
+//   ints[2] k_le = #{s : T_s <= observed}
+//   ints[3], ints[4] the two middle totals of the sorted T, at ranks
+//           floor((N - 1) / 2) and floor(N / 2) (equal for odd N); the median
+//           is their mean
+//   dbl[0] enrichment p = (k_ge + 1) / (N + 1)
+//   dbl[1] depletion p  = (k_le + 1) / (N + 1)
+//   dbl[2] Fig. 3's enrichment score log2(observed / median), evaluated as
+//          log2(double(2 * observed) / double(lo + hi)) (IEEE: 0 / 0 is NaN,
+//          x / 0 is +inf, log2(0) is -inf).
+// N = 0 gives zero middles and p = 1.  Returns 1 on 64-bit overflow of
+// 2 * observed or lo + hi.
+int or_mc_summary(const uint64_t* totals, uint64_t n, uint64_t observed, uint64_t* ints,
+                  double* dbl) {
+  std::vector<uint64_t> t(totals, totals + n);
+  std::sort(t.begin(), t.end());
+  uint64_t kge = 0, kle = 0;
+  for (uint64_t v : t) {
+    kge += v >= observed;
+#ifdef ORACLE_MUTANT_DEPLETE
+    kle += v < observed;  // planted: strict depletion tally
+#else
+    kle += v <= observed;
+#endif
+  }
+#ifdef ORACLE_MUTANT_MEDIAN
+  const uint64_t lo = n ? t[n / 2] : 0, hi = n ? t[n / 2] : 0;  // planted: upper middle twice
+#else
+  const uint64_t lo = n ? t[(n - 1) / 2] : 0, hi = n ? t[n / 2] : 0;
+#endif
+  if (observed > UINT64_MAX / 2 || lo > UINT64_MAX - hi) return 1;
+  ints[0] = observed;
+  ints[1] = kge;
+  ints[2] = kle;
+  ints[3] = lo;
+  ints[4] = hi;
+  dbl[0] = double(kge + 1) / double(n + 1);
+  dbl[1] = double(kle + 1) / double(n + 1);
+  dbl[2] = std::log2(double(2 * observed) / double(lo + hi));
   return 0;
 }
 

@@ -60,3 +60,22 @@ def read_projection_fixture():
     start = np.array([r[1] for r in rows], np.uint32)
     end = np.array([r[2] for r in rows], np.uint32)
     return co, cl_, chrom, start, end, [r[3] for r in rows], [r[4] for r in rows]
+
+
+def read_mc_summary_fixture():
+    """Rows of (observed, totals, expected dict) from mc_summary.txt."""
+    from fractions import Fraction
+    rows = []
+    with open(os.path.join(GOLDEN, "mc_summary.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            head, tot, tail = [x.split() for x in line.split("|")]
+            assert head[0] == "S"
+            v = tail
+            rows.append((int(head[1]), np.array([int(x) for x in tot], np.uint64), {
+                "k_ge": int(v[0]), "k_le": int(v[1]), "median_lo": int(v[2]),
+                "median_hi": int(v[3]), "p_enrich": Fraction(v[4]), "p_deplete": Fraction(v[5]),
+                "score": v[6]}))
+    return rows

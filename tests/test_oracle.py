@@ -14,7 +14,8 @@ import pytest
 
 import bits_synth as synth
 import oracle
-from goldens import read_count_fixture, read_philox_kat, read_projection_fixture
+from goldens import (read_count_fixture, read_mc_summary_fixture, read_philox_kat,
+                     read_projection_fixture)
 
 O = oracle.get()
 
@@ -243,6 +244,82 @@ def test_mc_tally_and_pvalue():
     assert (tz == 0).all() and oz == 0 and kz == 9 and pz == 1.0
 
 
+# ------------------------------------------- MC summary and per-set streams (Sec. 3.2, 3.3)
+
+def _score_ok(got: float, spec: str) -> bool:
+    import math
+    from fractions import Fraction
+    if spec == "nan":
+        return math.isnan(got)
+    if spec in ("inf", "-inf"):
+        return got == float(spec)
+    r = Fraction(spec)
+    return got == math.log2(r.numerator / r.denominator)
+
+
+def test_mc_summary_golden():
+    for obs, totals, exp in read_mc_summary_fixture():
+        got = O.mc_summary(totals, obs)
+        for k in ("k_ge", "k_le", "median_lo", "median_hi"):
+            assert got[k] == exp[k], (obs, list(totals), k)
+        assert got["p_enrich"] == exp["p_enrich"].numerator / exp["p_enrich"].denominator
+        assert got["p_deplete"] == exp["p_deplete"].numerator / exp["p_deplete"].denominator
+        assert _score_ok(got["log2_enrichment"], exp["score"]), (obs, list(totals))
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 100, 10_000, 10_001])
+def test_mc_summary_properties(n):
+    rng = np.random.default_rng(n)
+    t = rng.integers(1000, 1100, size=n).astype(np.uint64)
+    obs = int(rng.integers(990, 1110))
+    got = O.mc_summary(t, obs)
+    # Library median (mean of the two middles for even n) and counting identities.
+    assert (got["median_lo"] + got["median_hi"]) / 2 == np.median(t.astype(np.float64))
+    assert got["median_lo"] <= got["median_hi"]
+    assert got["k_ge"] + got["k_le"] == n + int((t == obs).sum())
+    assert got["k_ge"] == int((t >= obs).sum())
+    # Shuffle order does not matter.
+    got2 = O.mc_summary(rng.permutation(t), obs)
+    assert got2 == got or (np.isnan(got["log2_enrichment"]) and np.isnan(got2["log2_enrichment"]))
+    # The score doubles the ratio when observed doubles: log2 grows by exactly 1
+    # whenever the ratio stays in the normal double range.
+    g4 = O.mc_summary(t, 2 * obs)
+    assert g4["log2_enrichment"] == pytest.approx(got["log2_enrichment"] + 1.0, abs=1e-12)
+
+
+def test_mc_summary_empty_and_overflow():
+    got = O.mc_summary(np.zeros(0, np.uint64), 7)
+    assert got["k_ge"] == 0 and got["p_enrich"] == 1.0 and got["p_deplete"] == 1.0
+    with pytest.raises(ValueError):
+        O.mc_summary(np.array([2**63, 2**63], np.uint64), 1)
+
+
+def test_mc_set_index_streams():
+    # Set 0 is the single test's stream (pinned by the known-answer placement);
+    # set i reads its Philox block at counter word 2 = i.
+    genome = synth.single_contig(1000)
+    co, cl = synth.mc_contig_table(genome)
+    a = np.array([[7, 17], [100, 140], [0, 1000]], np.uint32)
+    np.testing.assert_array_equal(O.mc_place(a, co, cl, 9, 4), O.mc_place(a, co, cl, 9, 4, 0))
+    for set_index in (1, 5, 2**31 + 3):
+        out = O.mc_place(a, co, cl, seed=9, s=4, set_index=set_index)
+        for k in range(a.shape[0]):
+            x = O.philox([k, 4, set_index, 0], [9, 0])
+            u = (int(x[1]) << 32) | int(x[0])
+            ln = int(a[k, 1] - a[k, 0])
+            start = (u * (1000 - ln + 1)) >> 64
+            assert (int(out[k, 0]), int(out[k, 1])) == (start, start + ln)
+        assert not np.array_equal(out[:2], O.mc_place(a, co, cl, 9, 4)[:2])
+    # Totals of set i are recounts of set i's placements.
+    g3, a3, b3 = synth.config3(n_a=200, n_b=2000, n_hot=40)
+    co3, cl3 = synth.mc_contig_table(g3)
+    bs, be = O.build(b3)
+    tot, obs, _, _ = O.mc(a3, co3, cl3, bs, be, seed=3, s_begin=2, s_end=6, set_index=7)
+    for j, s_ in enumerate(range(2, 6)):
+        _, t = O.count_brute(O.mc_place(a3, co3, cl3, 3, s_, 7), b3)
+        assert tot[j] == t
+
+
 # ------------------------------------------------ projection and closed intervals (Sec. 1.1, 2.3)
 
 def _expected_rows(rows):
@@ -335,7 +412,8 @@ def test_projection_rejects_and_edges():
 MUTANTS = ["ORACLE_MUTANT_CLOSED", "ORACLE_MUTANT_LAST_LOWER", "ORACLE_MUTANT_PHILOX",
            "ORACLE_MUTANT_SCALE", "ORACLE_MUTANT_WORD_ORDER", "ORACLE_MUTANT_TALLY",
            "ORACLE_MUTANT_PROJECT_OFFSET", "ORACLE_MUTANT_PROJECT_CLOSED",
-           "ORACLE_MUTANT_BRUTE_CLOSED"]
+           "ORACLE_MUTANT_BRUTE_CLOSED", "ORACLE_MUTANT_DEPLETE", "ORACLE_MUTANT_MEDIAN",
+           "ORACLE_MUTANT_SET_WORD"]
 
 
 def _pins_pass(o: oracle.Oracle) -> bool:
@@ -368,6 +446,13 @@ def _pins_pass(o: oracle.Oracle) -> bool:
         a, b, exp, total = read_count_fixture("closed.txt")
         c, t = o.count_brute_closed(a, b)
         assert (c == exp).all() and t == total
+        for obs, totals, exp in read_mc_summary_fixture():
+            got = o.mc_summary(totals, obs)
+            assert all(got[k] == exp[k] for k in ("k_ge", "k_le", "median_lo", "median_hi"))
+        x = o.philox([1, 4, 5, 0], [9, 0])
+        u = (int(x[1]) << 32) | int(x[0])
+        placed = o.mc_place(np.array([[3, 4], [0, 10]], np.uint32), [0], [1000], 9, 4, 5)
+        assert int(placed[1, 0]) == (u * 991) >> 64
         return True
     except AssertionError:
         return False
