@@ -269,3 +269,30 @@ def unit_tiles(m: int, base: int = 0) -> np.ndarray:
 def mc_contig_table(genome: Genome):
     """(offsets, lengths) as uint32 arrays, the form the MC calls take."""
     return genome.offsets.copy(), genome.lengths.copy()
+
+
+def local_intervals(genome: Genome, n: int, seed: int, lo: int = 50, hi: int = 400,
+                    closed: bool = False, bad_frac: float = 0.0):
+    """Chromosome-local intervals in the form a BED file holds them.
+
+    Returns uint32 arrays (contig id, start, end).  The chromosome is chosen
+    with probability proportional to its length and the start is uniform
+    over the positions where an interval of length U[lo, hi] fits; for
+    closed output the end is start + length - 1.  A fraction ``bad_frac`` of
+    rows is then spoiled in one of three ways picked at random: a contig id
+    past the table, a start after the end, or an end past the contig.
+    """
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(lo, hi + 1, size=n, dtype=np.int64)
+    clen = genome.lengths.astype(np.int64)
+    contig = rng.choice(genome.n_contigs, size=n, p=clen / clen.sum())
+    start = rng.integers(0, clen[contig] - lens + 1)
+    end = start + lens - (1 if closed else 0)
+    if bad_frac > 0 and n:
+        bad = np.flatnonzero(rng.random(n) < bad_frac)
+        kind = rng.integers(0, 3, size=bad.shape[0])
+        k0, k1, k2 = bad[kind == 0], bad[kind == 1], bad[kind == 2]
+        contig[k0] = genome.n_contigs + rng.integers(0, 1000, size=k0.shape[0])
+        start[k1] = end[k1] + rng.integers(1, 50, size=k1.shape[0])
+        end[k2] = clen[contig[k2]] + rng.integers(0, 50, size=k2.shape[0])
+    return contig.astype(np.uint32), start.astype(np.uint32), end.astype(np.uint32)

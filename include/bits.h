@@ -135,6 +135,33 @@ bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
                               uint64_t* d_matrix, void* stream);
 
 /*
+ * bits_project -- the mapping of Sec. 2.3 that places every chromosome after
+ * the previous ones on one genome-wide line, and the conversion of closed
+ * intervals (Sec. 1.1 states its predicate for closed [start, end]) to the
+ * half-open form every other call takes: [s, e] on the integers is
+ * [s, e + 1).  Interval i on chromosome c = d_contig[i] becomes
+ * [off[c] + start_i, off[c] + end_i), plus one on the end when closed.
+ *   d_contig      device uint32[n], chromosome ids; ignored (may be NULL) when
+ *                 n_contigs == 0, which means one line at offset 0 with
+ *                 length 2^32 - 1.
+ *   d_start, d_end  device uint32[n], coordinates local to the chromosome.
+ *   d_contig_off, d_contig_len  device uint32[n_contigs].
+ *   closed        0: input is half-open [start, end); 1: closed [start, end].
+ *   d_out         device, n (start, end) uint32 pairs, 8-byte aligned; must
+ *                 not overlap the inputs.
+ *   d_n_rejected  device uint64[1] or NULL: set to the number of rejected rows.
+ * A row is rejected when its chromosome id is >= n_contigs, start > end, its
+ * half-open end passes the chromosome's length, or the projected end passes
+ * 2^32 - 1.  It is written as the inverted pair (2^32 - 1, 0), which
+ * bits_build_db and every counting call reject (BITS_EINVAL), so a rejected
+ * row cannot be counted by mistake.  Asynchronous; one kernel launch.
+ */
+bits_status bits_project(const uint32_t* d_contig, const uint32_t* d_start, const uint32_t* d_end,
+                         uint64_t n, const uint32_t* d_contig_off, const uint32_t* d_contig_len,
+                         uint32_t n_contigs, int32_t closed, uint32_t* d_out,
+                         uint64_t* d_n_rejected, void* stream);
+
+/*
  * bits_sort_intervals_noalloc -- the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory: code whose device
  * memory is entirely owned by another allocator (a framework's caching pool

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (METHOD_AUTO, METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, BitsError,
                    LIB_PATH)
 
-__all__ = ["Database", "count_matrix", "kernel_launches", "BitsError", "METHOD_AUTO",
+__all__ = ["Database", "count_matrix", "project", "kernel_launches", "BitsError", "METHOD_AUTO",
            "METHOD_SEARCH", "METHOD_RMI", "METHOD_MERGEPATH", "LIB_PATH", "device_view"]
 
 _U32 = (torch.uint32, torch.int32)
@@ -175,6 +175,46 @@ def count_matrix(dbs, a_sets, *, out: torch.Tensor | None = None, stream=None) -
                                _stream_ptr(stream))
     _lib.check(st, "bits_count_matrix")
     return out
+
+
+def project(start: torch.Tensor, end: torch.Tensor, *, contig: torch.Tensor | None = None,
+            contig_off: torch.Tensor | None = None, contig_len: torch.Tensor | None = None,
+            closed: bool = False, out: torch.Tensor | None = None, stream=None):
+    """Map chromosome-local (optionally closed) intervals onto the half-open
+    genome-wide line (Sec. 2.3).  Returns ``(intervals (n, 2) uint32, n_rejected)``
+    where ``n_rejected`` is a 1-element uint64 device tensor; rejected rows are
+    ``(2^32 - 1, 0)``.  Without a contig table the line is one contig at 0."""
+    lib = _lib.load()
+    s = _u32_vec(start, "start")
+    e = _u32_vec(end, "end")
+    n = int(s.numel())
+    if e.numel() != n:
+        raise ValueError("start and end differ in length")
+    nc = 0
+    cp = op = lp = None
+    if contig_off is not None or contig_len is not None or contig is not None:
+        if contig is None or contig_off is None or contig_len is None:
+            raise ValueError("contig, contig_off and contig_len go together")
+        c = _u32_vec(contig, "contig")
+        co = _u32_vec(contig_off, "contig_off")
+        cl = _u32_vec(contig_len, "contig_len")
+        if c.numel() != n or co.numel() != cl.numel():
+            raise ValueError("contig ids or contig table have the wrong length")
+        nc = int(co.numel())
+        cp = c.data_ptr() if n else None
+        op, lp = co.data_ptr(), cl.data_ptr()
+    if out is None:
+        out = torch.empty((n, 2), dtype=torch.uint32, device=s.device)
+    else:
+        out = _intervals(out, "out")
+        if out.shape[0] != n:
+            raise ValueError("out has the wrong number of rows")
+    rej = torch.empty(1, dtype=torch.uint64, device=s.device)
+    st = lib.bits_project(cp, s.data_ptr() if n else None, e.data_ptr() if n else None, n, op, lp,
+                          nc, 1 if closed else 0, out.data_ptr() if n else None, rej.data_ptr(),
+                          _stream_ptr(stream))
+    _lib.check(st, "bits_project")
+    return out, rej
 
 
 def kernel_launches() -> int:

@@ -20,7 +20,7 @@ METHOD_AUTO, METHOD_SEARCH, METHOD_RMI, METHOD_MERGEPATH = range(4)
 # Every symbol include/bits.h declares.
 EXPORTS = ["bits_build_db", "bits_count", "bits_count_method", "bits_mc", "bits_count_matrix",
            "bits_db_info", "bits_check", "bits_free", "bits_last_error", "bits_kernel_launches",
-           "bits_sort_intervals_noalloc", "bits_db_rmi", "bits_selftest_wait"]
+           "bits_sort_intervals_noalloc", "bits_db_rmi", "bits_selftest_wait", "bits_project"]
 
 
 class BitsError(RuntimeError):
@@ -60,11 +60,13 @@ def load():
     lib.bits_check.argtypes = [vp, vp]
     lib.bits_sort_intervals_noalloc.argtypes = [u32p, C.c_uint64, u32p, u32p, vp]
     lib.bits_selftest_wait.argtypes = [C.c_uint32, vp]
+    lib.bits_project.argtypes = [u32p, u32p, u32p, C.c_uint64, u32p, u32p, C.c_uint32, C.c_int32,
+                                 u32p, u64p, vp]
     lib.bits_db_rmi.argtypes = [vp, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                 C.POINTER(C.c_float), C.POINTER(C.c_float)]
     for f in ("bits_build_db", "bits_count", "bits_count_method", "bits_mc", "bits_count_matrix",
               "bits_db_info", "bits_check", "bits_sort_intervals_noalloc", "bits_db_rmi",
-              "bits_selftest_wait"):
+              "bits_selftest_wait", "bits_project"):
         getattr(lib, f).restype = st
     lib.bits_free.argtypes = [vp]
     lib.bits_free.restype = None

@@ -14,6 +14,7 @@
 #include "rmi.cuh"
 #include "allpairs.cuh"
 #include "mergepath.cuh"
+#include "project.cuh"
 
 namespace bits {
 namespace {
@@ -283,6 +284,35 @@ bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
   }
   return run_count_matrix(dbs, n_db, d_as, n_as, n_sets, d_matrix,
                           static_cast<cudaStream_t>(stream));
+}
+
+bits_status bits_project(const uint32_t* d_contig, const uint32_t* d_start, const uint32_t* d_end,
+                         uint64_t n, const uint32_t* d_contig_off, const uint32_t* d_contig_len,
+                         uint32_t n_contigs, int32_t closed, uint32_t* d_out,
+                         uint64_t* d_n_rejected, void* stream) {
+  if (n >= (1ull << 32)) {
+    set_error("bits_project: n must be below 2^32");
+    return BITS_EOVERFLOW;
+  }
+  if (closed != 0 && closed != 1) {
+    set_error("bits_project: closed must be 0 or 1");
+    return BITS_EINVAL;
+  }
+  if (n && (!d_start || !d_end || !d_out || (n_contigs && !d_contig))) {
+    set_error("bits_project: NULL interval array");
+    return BITS_EINVAL;
+  }
+  if (n_contigs && (!d_contig_off || !d_contig_len)) {
+    set_error("bits_project: NULL contig table");
+    return BITS_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(d_out) & 7u) || (reinterpret_cast<uintptr_t>(d_start) & 3u) ||
+      (reinterpret_cast<uintptr_t>(d_end) & 3u) || (reinterpret_cast<uintptr_t>(d_contig) & 3u)) {
+    set_error("bits_project: misaligned pointer (out needs 8 bytes, inputs 4)");
+    return BITS_EINVAL;
+  }
+  return launch_project(d_contig, d_start, d_end, n, d_contig_off, d_contig_len, n_contigs,
+                        closed != 0, d_out, d_n_rejected, static_cast<cudaStream_t>(stream));
 }
 
 bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_t** d_be,
