@@ -56,11 +56,14 @@ def _declare(lib):
                               C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, u64p, u64p, u64p,
                               C.POINTER(C.c_double), C.c_int]
     lib.or_mc_summary.argtypes = [u64p, C.c_uint64, C.c_uint64, u64p, C.POINTER(C.c_double)]
+    lib.or_enumerate_brute.argtypes = [u32p, C.c_uint64, u32p, C.c_uint64, u64p, u32p]
+    lib.or_enumerate_scan.argtypes = [u32p, C.c_uint64, u32p, C.c_uint64, u64p, u32p]
     lib.or_count_brute_closed.argtypes = [u32p, C.c_uint64, u32p, C.c_uint64, u32p, u64p]
     lib.or_project.argtypes = [u32p, u32p, u32p, C.c_uint64, u32p, u32p, C.c_uint32, C.c_int, u32p]
     lib.or_project.restype = C.c_uint64
     for f in ("or_count_brute", "or_build", "or_count_sorted", "or_mc_place", "or_mc",
-              "or_count_brute_closed", "or_mc_place_set", "or_mc_set", "or_mc_summary"):
+              "or_count_brute_closed", "or_mc_place_set", "or_mc_set", "or_mc_summary",
+              "or_enumerate_brute", "or_enumerate_scan"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -132,6 +135,24 @@ class Oracle:
                                   _p32(co) if co.size else nil, _p32(cl) if cl.size else nil,
                                   co.shape[0], 1 if closed else 0, _p32(out))
         return out, int(bad)
+
+    def _enumerate(self, fn, a, b):
+        a, b = _iv(a), _iv(b)
+        off = np.zeros(a.shape[0] + 1, np.uint64)
+        nil = C.cast(0, C.POINTER(C.c_uint32))
+        if fn(_p32(a), a.shape[0], _p32(b), b.shape[0], _p64(off), nil):
+            raise ValueError("oracle rejected input")
+        pairs = np.zeros((int(off[-1]), 2), np.uint32)
+        fn(_p32(a), a.shape[0], _p32(b), b.shape[0], _p64(off), _p32(pairs) if pairs.size else nil)
+        return off, pairs
+
+    def enumerate_brute(self, a, b):
+        """(offsets uint64[n+1], pairs uint32[total, 2]) by the definition, (i, j) order."""
+        return self._enumerate(self.lib.or_enumerate_brute, a, b)
+
+    def enumerate_scan(self, a, b):
+        """Same pairs by the start-sorted scan terminated at ICount, in scan order."""
+        return self._enumerate(self.lib.or_enumerate_scan, a, b)
 
     def build(self, b):
         b = _iv(b)

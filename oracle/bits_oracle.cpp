@@ -329,6 +329,76 @@ int or_mc_summary(const uint64_t* totals, uint64_t n, uint64_t observed, uint64_
   return 0;
 }
 
+// Enumeration problem (Sec. 1.1: report every intersecting pair), by the
+// definition: for each query i in order, every database interval j in index
+// order with b_j meeting a_i.  offsets[i] is the first pair of query i and
+// offsets[na] the number of pairs; pairs (if not NULL) receives (i, j) words.
+int or_enumerate_brute(const uint32_t* a, uint64_t na, const uint32_t* b, uint64_t nb,
+                       uint64_t* offsets, uint32_t* pairs) {
+  if (check_db(b, nb) || check_queries(a, na)) return 1;
+  uint64_t k = 0;
+  for (uint64_t i = 0; i < na; ++i) {
+    offsets[i] = k;
+    for (uint64_t j = 0; j < nb; ++j)
+      if (intersects(a[2 * i], a[2 * i + 1], b[2 * j], b[2 * j + 1])) {
+        if (pairs) {
+          pairs[2 * k] = uint32_t(i);
+          pairs[2 * k + 1] = uint32_t(j);
+        }
+        ++k;
+      }
+  }
+  offsets[na] = k;
+  return 0;
+}
+
+// Enumeration the way Sec. 2.2 sets it up: B sorted by start (ties in index
+// order) with each entry's end and index beside it; ICount gives the number
+// c of intervals meeting a, and since every one of them starts before
+// a.end, scanning the entries left of first = #(B_S < a.end) from right to
+// left and keeping those with end > a.start finds all of them; the scan
+// stops at the c-th (|I| as the termination condition).  Pairs of a query
+// come in scan order: descending start, then descending index.
+int or_enumerate_scan(const uint32_t* a, uint64_t na, const uint32_t* b, uint64_t nb,
+                      uint64_t* offsets, uint32_t* pairs) {
+  if (check_db(b, nb) || check_queries(a, na)) return 1;
+  std::vector<uint32_t> bs(nb), be(nb), idx(nb);
+  for (uint64_t j = 0; j < nb; ++j) {
+    bs[j] = b[2 * j];
+    be[j] = b[2 * j + 1];
+    idx[j] = uint32_t(j);
+  }
+  std::sort(bs.begin(), bs.end());
+  std::sort(be.begin(), be.end());
+  std::stable_sort(idx.begin(), idx.end(),
+                   [&](uint32_t x, uint32_t y) { return b[2 * x] < b[2 * y]; });
+  uint64_t k = 0;
+  for (uint64_t i = 0; i < na; ++i) {
+    offsets[i] = k;
+    const uint32_t as = a[2 * i], ae = a[2 * i + 1];
+    const uint32_t c = icount(bs.data(), be.data(), nb, as, ae);
+    const uint64_t first = std::lower_bound(bs.begin(), bs.end(), ae) - bs.begin();
+    uint32_t found = 0;
+    for (uint64_t p = first; p > 0 && found < c; --p) {
+      const uint32_t j = idx[p - 1];
+#ifdef ORACLE_MUTANT_ENUM_END
+      if (b[2 * j + 1] >= as) {  // planted: touching ends counted as hits
+#else
+      if (b[2 * j + 1] > as) {
+#endif
+        if (pairs) {
+          pairs[2 * (k + found)] = uint32_t(i);
+          pairs[2 * (k + found) + 1] = j;
+        }
+        ++found;
+      }
+    }
+    k += c;
+  }
+  offsets[na] = k;
+  return 0;
+}
+
 // Sec. 1.1's predicate exactly as printed, for closed intervals [start, end]:
 // a and b intersect iff a.start <= b.end and a.end >= b.start.  Brute force.
 int or_count_brute_closed(const uint32_t* a, uint64_t na, const uint32_t* b, uint64_t nb,

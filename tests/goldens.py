@@ -79,3 +79,15 @@ def read_mc_summary_fixture():
                 "median_hi": int(v[3]), "p_enrich": Fraction(v[4]), "p_deplete": Fraction(v[5]),
                 "score": v[6]}))
     return rows
+
+
+def read_enumerate_fixture():
+    """(A, B, expected counts, total, partner lists in scan order) from enumerate.txt."""
+    a, b, exp, total = read_count_fixture("enumerate.txt")
+    partners = {}
+    with open(os.path.join(GOLDEN, "enumerate.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line and line[0] == "E":
+                partners[int(line[1])] = [int(x) for x in line[2:]]
+    return a, b, exp, total, [partners[i] for i in range(a.shape[0])]

@@ -14,8 +14,8 @@ import pytest
 
 import bits_synth as synth
 import oracle
-from goldens import (read_count_fixture, read_mc_summary_fixture, read_philox_kat,
-                     read_projection_fixture)
+from goldens import (read_count_fixture, read_enumerate_fixture, read_mc_summary_fixture,
+                     read_philox_kat, read_projection_fixture)
 
 O = oracle.get()
 
@@ -244,6 +244,54 @@ def test_mc_tally_and_pvalue():
     assert (tz == 0).all() and oz == 0 and kz == 9 and pz == 1.0
 
 
+# ------------------------------------------------------- enumeration (Sec. 1.1, Sec. 2.2)
+
+def _partners(off, pairs, i):
+    return [int(x) for x in pairs[int(off[i]):int(off[i + 1]), 1]]
+
+
+def test_enumerate_golden():
+    a, b, exp, total, scan_lists = read_enumerate_fixture()
+    for fn, ordered in ((O.enumerate_scan, True), (O.enumerate_brute, False)):
+        off, pairs = fn(a, b)
+        assert int(off[-1]) == total == pairs.shape[0]
+        np.testing.assert_array_equal(np.diff(off.astype(np.int64)), exp)
+        for i, want in enumerate(scan_lists):
+            got = _partners(off, pairs, i)
+            assert got == (want if ordered else sorted(want)), (fn.__name__, i)
+            assert (pairs[int(off[i]):int(off[i + 1]), 0] == i).all()
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_enumerate_scan_matches_definition(seed):
+    a, b = synth.tiny_random(seed, n_a=60, n_b=80, coord_max=200, max_len=40)
+    ob, pb = O.enumerate_brute(a, b)
+    os_, ps = O.enumerate_scan(a, b)
+    np.testing.assert_array_equal(ob, os_)
+    counts, _ = O.count_brute(a, b)
+    np.testing.assert_array_equal(np.diff(ob.astype(np.int64)), counts)
+    bstart = b[:, 0].astype(np.int64)
+    for i in range(a.shape[0]):
+        got = _partners(os_, ps, i)
+        assert sorted(got) == _partners(ob, pb, i)
+        # scan order: descending start, equal starts in descending index
+        keys = [(-bstart[j], -j) for j in got]
+        assert keys == sorted(keys)
+
+
+def test_enumerate_nested_closed_form():
+    # [i, 2m-i) for i < m: the point query [x, x+1) meets min(x+1, 2m-x) of
+    # them, the innermost ones; the scan walks past none of the others.
+    m = 30
+    b = synth.nested(m)
+    x = np.arange(0, 2 * m + 3)
+    a = np.stack([x, x + 1], 1).astype(np.uint32)
+    off, pairs = O.enumerate_scan(a, b)
+    for i, xi in enumerate(x):
+        want = set(range(0, min(xi + 1, 2 * m - xi))) if xi < 2 * m else set()
+        assert set(_partners(off, pairs, i)) == want
+
+
 # ------------------------------------------- MC summary and per-set streams (Sec. 3.2, 3.3)
 
 def _score_ok(got: float, spec: str) -> bool:
@@ -413,7 +461,7 @@ MUTANTS = ["ORACLE_MUTANT_CLOSED", "ORACLE_MUTANT_LAST_LOWER", "ORACLE_MUTANT_PH
            "ORACLE_MUTANT_SCALE", "ORACLE_MUTANT_WORD_ORDER", "ORACLE_MUTANT_TALLY",
            "ORACLE_MUTANT_PROJECT_OFFSET", "ORACLE_MUTANT_PROJECT_CLOSED",
            "ORACLE_MUTANT_BRUTE_CLOSED", "ORACLE_MUTANT_DEPLETE", "ORACLE_MUTANT_MEDIAN",
-           "ORACLE_MUTANT_SET_WORD"]
+           "ORACLE_MUTANT_SET_WORD", "ORACLE_MUTANT_ENUM_END"]
 
 
 def _pins_pass(o: oracle.Oracle) -> bool:
@@ -453,6 +501,12 @@ def _pins_pass(o: oracle.Oracle) -> bool:
         u = (int(x[1]) << 32) | int(x[0])
         placed = o.mc_place(np.array([[3, 4], [0, 10]], np.uint32), [0], [1000], 9, 4, 5)
         assert int(placed[1, 0]) == (u * 991) >> 64
+        a, b, exp, total, scan_lists = read_enumerate_fixture()
+        off, pairs = o.enumerate_scan(a, b)
+        assert [_partners(off, pairs, i) for i in range(a.shape[0])] == scan_lists
+        off, pairs = o.enumerate_brute(a, b)
+        assert [_partners(off, pairs, i) for i in range(a.shape[0])] == \
+            [sorted(x) for x in scan_lists]
         return True
     except AssertionError:
         return False
