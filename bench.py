@@ -350,6 +350,31 @@ def run_ours(args):
                             "kernel": "k_project<true>", "algorithmic_bytes_per_interval": 20}}
     del pc, ps, pe, p_out
 
+    # ---- enumeration (Sec. 1.1): every pair of the exome-vs-reads workload ----
+    db_en = bits.Database(b, enumerate=True)
+
+    def enum_step():
+        db_en.enumerate(a, check=False)
+
+    en_ms, en_launches, _ = timed(enum_step, args.steps, args.warmup)
+    db_en.check()
+    off_g, pairs_g = db_en.enumerate(a)
+    idx = np.random.default_rng(2).choice(n_a, size=64, replace=False)
+    eoff, epairs = o.enumerate_scan(a_np[idx], b_np)
+    off_np, pairs_np = off_g.cpu().numpy(), pairs_g.cpu().numpy()
+    en_ok = True
+    for k, i in enumerate(idx):
+        got = pairs_np[int(off_np[i]):int(off_np[i + 1]), 1]
+        en_ok &= bool(np.array_equal(got, epairs[int(eoff[k]):int(eoff[k + 1]), 1]))
+    n_pairs = int(off_np[-1])
+    enumerate_ = {"ms": en_ms, "queries": n_a, "pairs": n_pairs,
+                  "queries_per_s": world * n_a / (en_ms * 1e-3),
+                  "pairs_per_s": world * n_pairs / (en_ms * 1e-3), "gpu_launches": en_launches,
+                  "parity_sample_ok": en_ok,
+                  "note": "offsets pass (count + scan), one read of the pair count, pairs pass"}
+    db_en.free()
+    del off_g, pairs_g
+
     # ---- Monte-Carlo test (Sec. 3.2): 100k vs 1M, 10,000 shuffles per launch --
     g3, a3_np, b3_np = bits_synth.config3()
     co_np, cl_np = bits_synth.mc_contig_table(g3)
@@ -378,8 +403,8 @@ def run_ours(args):
     # The MC kernel is bound by instruction issue (its database stays in L2):
     # roofline = warp instructions issued per second against one warp
     # instruction per clock per scheduler (148 SMs x 4) at the sampled clock.
-    mc_src = ["paper_1208_3407_b300/csrc/mc.cu", "paper_1208_3407_b300/csrc/search.cuh",
-              "paper_1208_3407_b300/csrc/philox.cuh"]
+    mc_src = ["paper_1208_3407_b300/csrc/mc.cu", "paper_1208_3407_b300/csrc/mc_unit.cuh",
+              "paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/philox.cuh"]
     wi = profiled_value("k_mc_search", "warp_instructions_per_launch", mc_src)
     mc_roof = None
     if wi is not None and clocks.get("sm_mhz"):
@@ -467,9 +492,58 @@ def run_ours(args):
                 "parity_sample_ok": bool(all(checks)),
                 "paper_context": "Sec. 3.3: 159 x 159 tracks, about 4e9 intervals per iteration, "
                                  "9,069 minutes for 1e4 iterations on one 2012 GPU"}
+    # ---- Monte-Carlo screen (Sec. 3.3): every pair re-placed and recounted ----
+    # The same 64 x 32 sets, 4 shuffles of every query set per step against
+    # all 32 databases (1.4e10 placements); the paper's screen ran 1e4.
+    co5, cl5 = bits_synth.mc_contig_table(g5)
+    dco5, dcl5 = to_dev(co5), to_dev(cl5)
+    nsh5 = 4
+    scr_out = (torch.empty((len(a5), len(dbs5)), dtype=torch.uint64, device=dev),
+               torch.empty((len(a5), len(dbs5), nsh5), dtype=torch.uint64, device=dev),
+               torch.empty((len(a5), len(dbs5), 8), dtype=torch.uint64, device=dev))
+
+    def screen_step():
+        bits.mc_matrix(dbs5, a5, dco5, dcl5, seed=17, shuffle_end=nsh5, out=scr_out)
+
+    screen_step()                                  # builds and caches the launch graph
+    ms_scr, l_scr, _ = timed(screen_step, 3, 3)
+    for d in dbs5:
+        d.check()
+    i_s = int(np.argmin([x.shape[0] for x in a5_np]))
+    bs5, be5 = o.build(b5_np[7])
+    ot, oo, _, _ = o.mc(a5_np[i_s], co5, cl5, bs5, be5, seed=17, s_begin=0, s_end=nsh5,
+                        threads=os.cpu_count() or 1, set_index=i_s)
+    scr_ok = bool(np.array_equal(scr_out[1][i_s, 7].cpu().numpy(), ot) and
+                  int(scr_out[0][i_s, 7].cpu()) == oo)
+    placements = n_q5 * len(dbs5) * nsh5
+    # Issue-bound like the single test: warp instructions per placement from
+    # the ncu capture of the 16 x 8 screen, times this step's placements.
+    mm_src = ["paper_1208_3407_b300/csrc/mc_matrix.cu", "paper_1208_3407_b300/csrc/mc_unit.cuh",
+              "paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/philox.cuh"]
+    wi_m = profiled_value("k_mc_matrix_screen_16x8", "warp_instructions_per_launch", mm_src)
+    pl_m = profiled_value("k_mc_matrix_screen_16x8", "placements_per_launch", mm_src)
+    scr_roof = None
+    if wi_m is not None and pl_m and clocks.get("sm_mhz"):
+        issue_peak = 148 * 4 * clocks["sm_mhz"] * 1e6
+        ach = wi_m / pl_m * placements / (ms_scr * 1e-3)
+        scr_roof = {"bound": "alu", "achieved": ach, "peak": issue_peak,
+                    "unit": "warp-instructions/s", "frac": ach / issue_peak,
+                    "kernel": "k_mc_matrix",
+                    "peak_source": "148 SMs x 4 schedulers x 1 warp-instruction/clock at the "
+                                   "sampled SM clock; instructions per placement from the "
+                                   "16 x 8 capture"}
+    mc_screen = {"workload": "the all-pairs sets above, 4 shuffles per step of every query set "
+                             "against all 32 databases, plus the observed matrix and per-pair "
+                             "summary (tallies, median, Fig. 3 score)",
+                 "ms_per_step": ms_scr, "shuffles_per_step": nsh5,
+                 "placements_per_s": world * placements / (ms_scr * 1e-3),
+                 "pair_shuffles_per_s": world * len(a5) * len(dbs5) * nsh5 / (ms_scr * 1e-3),
+                 "gpu_launches": l_scr, "parity_sample_ok": scr_ok, "roofline": scr_roof,
+                 "paper_context": "Sec. 3.3: 1e4 shuffles of the 159 x 159 screen in 9,069 "
+                                  "minutes on one 2012 GPU"}
     for d in dbs5:
         d.free()
-    del a5, m5
+    del a5, m5, scr_out
 
     sampler.stop()
 
@@ -525,9 +599,11 @@ def run_ours(args):
                   "with_learned_index_s": build_rmi_s},
         "parity_sample_ok": parity_ok,
         "project": project,
+        "enumerate": enumerate_,
         "mc": mc,
         "scale": scale,
         "allpairs": allpairs,
+        "mc_screen": mc_screen,
     }
     if rank == 0:
         print(json.dumps(line))

@@ -65,8 +65,12 @@ typedef struct bits_opts {
   int32_t top_tree_log2;   /* 0: default 12; the top level of each array's        */
                            /* 16-ary search tree kept in shared memory holds at   */
                            /* most 2^k - 1 keys, k in [2, 14]                     */
-  int32_t reserved;        /* must be 0                                           */
+  int32_t flags;           /* BITS_FLAG_* bits; 0 for none                        */
 } bits_opts;
+
+/* Keep the database intervals in start order as (end, index) pairs, 8 more
+ * bytes per interval, so that bits_enumerate_pairs can report pairs. */
+#define BITS_FLAG_ENUMERATE 1
 
 /*
  * bits_build_db -- Algorithm 2's set-up: B_S <- starts, B_E <- ends, sort both.
@@ -98,6 +102,32 @@ bits_status bits_count_method(const bits_db* db, int32_t method, const uint32_t*
                               uint64_t n, uint32_t* d_counts, uint64_t* d_total, void* stream);
 
 /*
+ * Enumeration problem (Sec. 1.1: report every intersecting pair), in two
+ * stream-ordered steps so that the caller can size the output in between.
+ *
+ * bits_enumerate_offsets -- d_offsets (device uint64[n + 1]) receives the
+ * exclusive prefix sum of ICount over the queries: query i's pairs occupy
+ * [d_offsets[i], d_offsets[i + 1]) and d_offsets[n] is the number of pairs.
+ * Asynchronous; inverted queries count 0 and set the device error word.
+ *
+ * bits_enumerate_pairs -- writes the pairs, as (query index, database
+ * interval index) uint32 pairs in d_pairs (device, 8-byte aligned,
+ * d_offsets[n] pairs), given the offsets of the same queries and database.
+ * Needs a database built with BITS_FLAG_ENUMERATE (else BITS_ENOTIMPL).  As
+ * Sec. 2.2 suggests, ICount ends the scan: the database intervals in start
+ * order left of first = #(B_S < a.end) are walked right to left and those
+ * with end > a.start kept until the count is reached, so a query's pairs
+ * come in descending start order (equal starts: descending index).  A query
+ * under a long interval that contains many others scans past them (the
+ * paper's containment case).  Asynchronous; offsets that do not match the
+ * queries set the device error word (bits_check: BITS_EINVAL).
+ */
+bits_status bits_enumerate_offsets(const bits_db* db, const uint32_t* d_a, uint64_t n,
+                                   uint64_t* d_offsets, void* stream);
+bits_status bits_enumerate_pairs(const bits_db* db, const uint32_t* d_a, uint64_t n,
+                                 const uint64_t* d_offsets, uint32_t* d_pairs, void* stream);
+
+/*
  * bits_mc -- Monte-Carlo significance test of Sec. 3.2.  Each shuffle s in
  * [shuffle_begin, shuffle_end) re-places every query interval uniformly inside
  * its own contig with its length kept, and recounts it against the fixed
@@ -120,6 +150,65 @@ bits_status bits_mc(const bits_db* db, int32_t method, const uint32_t* d_a, uint
                     uint32_t n_contigs, uint64_t seed, uint32_t shuffle_begin,
                     uint32_t shuffle_end, uint64_t* d_totals, uint64_t* h_observed,
                     uint64_t* h_k_ge, double* h_pvalue, void* stream);
+
+/*
+ * Summary of one Monte-Carlo test (64 bytes).  With N shuffled totals T_s:
+ *   k_ge, k_le    #{s : T_s >= observed}, #{s : T_s <= observed}
+ *   median_lo/hi  the sorted totals at ranks floor((N-1)/2) and floor(N/2)
+ *                 (equal for odd N); the median is their mean
+ *   p_enrich      (k_ge + 1) / (N + 1), one IEEE double division
+ *   p_deplete     (k_le + 1) / (N + 1)
+ *   log2_enrichment  Fig. 3's enrichment score log2(observed / median),
+ *                 evaluated as log2(double(2 * observed) / double(lo + hi))
+ *                 with IEEE specials (0/0 gives NaN, x/0 +inf, log2(0)
+ *                 -inf); NaN as well if 2 * observed or lo + hi overflows.
+ */
+typedef struct bits_mc_stat {
+  uint64_t observed;
+  uint64_t k_ge;
+  uint64_t k_le;
+  uint64_t median_lo;
+  uint64_t median_hi;
+  double p_enrich;
+  double p_deplete;
+  double log2_enrichment;
+} bits_mc_stat;
+
+/*
+ * bits_mc_summary -- bits_mc_stat of n_tests Monte-Carlo tests at once (the
+ * Sec. 3.2 tally in both directions and the Fig. 3 score).
+ *   d_totals    device uint64[n_tests][n_shuffles], row t = test t's totals.
+ *   d_observed  device uint64[n_tests].
+ *   d_stats     device bits_mc_stat[n_tests], 8-byte aligned.
+ * One CTA per test; asynchronous.  The score's log2 is CUDA's (at most 1 ulp
+ * from the exact value); every other field is exact.
+ */
+bits_status bits_mc_summary(const uint64_t* d_totals, uint32_t n_shuffles, uint32_t n_tests,
+                            const uint64_t* d_observed, bits_mc_stat* d_stats, void* stream);
+
+/*
+ * bits_mc_matrix -- the Monte-Carlo screen of Sec. 3.3: a significance test
+ * (Sec. 3.2) for every pair of query set A_i and database B_j.
+ *   dbs, n_db, d_as, n_as, n_sets   as bits_count_matrix.
+ *   d_contig_off, d_contig_len, n_contigs, seed, shuffle_begin, shuffle_end
+ *                as bits_mc; one contig table for every set (n_contigs <= 4096).
+ *   d_observed   device uint64[n_sets][n_db]: total(A_i, B_j) (bits_count_matrix).
+ *   d_totals     device uint64[n_sets][n_db][N], N = shuffle_end - shuffle_begin:
+ *                the total of shuffle s for pair (i, j) at [i][j][s - begin].
+ *   d_stats      device bits_mc_stat[n_sets][n_db], or NULL to skip.
+ * Interval k of set i in shuffle s draws Philox4x32-10 at counter
+ * (k, s, i, 0), so set i is re-placed the same way against every database and
+ * set 0 reproduces bits_mc.  Asynchronous: invalid query intervals set the
+ * error word of each database they were counted against (bits_check).  The
+ * shuffle work of all pairs is one persistent launch, replayed from a cached
+ * CUDA graph when the same arguments repeat.  Work units above 2^32 (about
+ * 1.1e15 placements) give BITS_EOVERFLOW: split the shuffle range.
+ */
+bits_status bits_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint32_t* const* d_as,
+                           const uint64_t* n_as, uint32_t n_sets, const uint32_t* d_contig_off,
+                           const uint32_t* d_contig_len, uint32_t n_contigs, uint64_t seed,
+                           uint32_t shuffle_begin, uint32_t shuffle_end, uint64_t* d_observed,
+                           uint64_t* d_totals, bits_mc_stat* d_stats, void* stream);
 
 /*
  * bits_count_matrix -- all-pairs screen of Sec. 3.3: M[i][j] = total(A_i, B_j).

@@ -19,7 +19,8 @@ from . import _lib
 from ._lib import (METHOD_AUTO, METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, BitsError,
                    LIB_PATH)
 
-__all__ = ["Database", "count_matrix", "project", "kernel_launches", "BitsError", "METHOD_AUTO",
+__all__ = ["Database", "count_matrix", "project", "mc_summary", "mc_matrix", "McStats",
+           "kernel_launches", "BitsError", "METHOD_AUTO",
            "METHOD_SEARCH", "METHOD_RMI", "METHOD_MERGEPATH", "LIB_PATH", "device_view"]
 
 _U32 = (torch.uint32, torch.int32)
@@ -63,11 +64,12 @@ class Database:
     """A BITS database: the sorted start and end arrays of B (Algorithm 2)."""
 
     def __init__(self, b: torch.Tensor, *, method: int = 0, rmi_leaves_log2: int = 0,
-                 top_tree_log2: int = 0, stream=None):
+                 top_tree_log2: int = 0, enumerate: bool = False, stream=None):
         b = _intervals(b, "b")
         self._lib = _lib.load()
         self.device = b.device
-        opts = _lib.Opts(method, rmi_leaves_log2, top_tree_log2, 0)
+        opts = _lib.Opts(method, rmi_leaves_log2, top_tree_log2,
+                         _lib.FLAG_ENUMERATE if enumerate else 0)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
             st = self._lib.bits_build_db(b.data_ptr() if b.numel() else None, b.shape[0],
@@ -123,6 +125,35 @@ class Database:
         if check:
             _lib.check(self._lib.bits_check(self._h, sp), "bits_count (device check)")
         return out, total
+
+    def enumerate(self, a: torch.Tensor, *, stream=None, check: bool = True):
+        """Every intersecting pair (Sec. 1.1's enumeration problem).
+
+        Returns ``(offsets, pairs)``: uint64 offsets of shape ``(n + 1,)`` (query
+        i's pairs are ``pairs[offsets[i]:offsets[i + 1]]``) and uint32 pairs of
+        shape ``(total, 2)`` holding (query index, database index), each
+        query's in descending database start order.  Needs a database built
+        with ``enumerate=True``.  Reads the pair count back to size the output
+        (one synchronisation)."""
+        a = _intervals(a, "a")
+        n = int(a.shape[0])
+        sp = _stream_ptr(stream)
+        off = torch.empty(n + 1, dtype=torch.uint64, device=a.device)
+        ap = a.data_ptr() if n else None
+        _lib.check(self._lib.bits_enumerate_offsets(self._h, ap, n, off.data_ptr(), sp),
+                   "bits_enumerate_offsets")
+        if stream is None:
+            total = int(off[n].item())
+        else:
+            with torch.cuda.stream(stream):
+                total = int(off[n].item())
+        pairs = torch.empty((total, 2), dtype=torch.uint32, device=a.device)
+        _lib.check(self._lib.bits_enumerate_pairs(self._h, ap, n, off.data_ptr(),
+                                                  pairs.data_ptr() if total else None, sp),
+                   "bits_enumerate_pairs")
+        if check:
+            _lib.check(self._lib.bits_check(self._h, sp), "bits_enumerate (device check)")
+        return off, pairs
 
     def check(self, stream=None):
         _lib.check(self._lib.bits_check(self._h, _stream_ptr(stream)), "bits_check")
@@ -215,6 +246,107 @@ def project(start: torch.Tensor, end: torch.Tensor, *, contig: torch.Tensor | No
                           _stream_ptr(stream))
     _lib.check(st, "bits_project")
     return out, rej
+
+
+class McStats:
+    """Device array of bits_mc_stat records (include/bits.h), 64 bytes each.
+
+    ``raw`` is a uint64 tensor of shape ``shape + (8,)``; the fields are views
+    of it: observed, k_ge, k_le, median_lo, median_hi (uint64) and p_enrich,
+    p_deplete, log2_enrichment (float64)."""
+
+    INTS = ("observed", "k_ge", "k_le", "median_lo", "median_hi")
+    DBLS = ("p_enrich", "p_deplete", "log2_enrichment")
+
+    def __init__(self, raw: torch.Tensor):
+        self.raw = raw
+
+    def __getattr__(self, name):
+        if name in McStats.INTS:
+            return self.raw[..., McStats.INTS.index(name)]
+        if name in McStats.DBLS:
+            return self.raw[..., 5 + McStats.DBLS.index(name)].view(torch.float64)
+        raise AttributeError(name)
+
+    def to_dicts(self):
+        """Host copies, one dict per test (row-major order)."""
+        h = self.raw.reshape(-1, 8).cpu()
+        ints = h[:, :5].tolist()
+        dbl = h[:, 5:].contiguous().view(torch.float64).tolist()
+        return [dict(zip(McStats.INTS + McStats.DBLS, [int(x) for x in i] + d))
+                for i, d in zip(ints, dbl)]
+
+
+def _u64(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype not in (torch.uint64, torch.int64):
+        raise TypeError(f"{name} must be a uint64/int64 CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return x
+
+
+def mc_summary(totals: torch.Tensor, observed: torch.Tensor, *, stream=None) -> McStats:
+    """Tallies, middle totals, p-values and Fig. 3 score of Monte-Carlo tests.
+
+    ``totals`` has shape ``(..., N)`` (one row of shuffled totals per test) and
+    ``observed`` the leading shape ``(...)``."""
+    lib = _lib.load()
+    totals = _u64(totals, "totals")
+    observed = _u64(observed, "observed")
+    shape = tuple(totals.shape[:-1])
+    if tuple(observed.shape) != shape:
+        raise ValueError("observed must have the shape of totals without its last axis")
+    n_tests = int(observed.numel())
+    n_sh = int(totals.shape[-1])
+    raw = torch.empty(shape + (8,), dtype=torch.uint64, device=totals.device)
+    st = lib.bits_mc_summary(totals.data_ptr() if totals.numel() else None, n_sh, n_tests,
+                             observed.data_ptr() if n_tests else None,
+                             raw.data_ptr() if n_tests else None, _stream_ptr(stream))
+    _lib.check(st, "bits_mc_summary")
+    return McStats(raw)
+
+
+def mc_matrix(dbs, a_sets, contig_off: torch.Tensor, contig_len: torch.Tensor, *, seed: int,
+              shuffle_begin: int = 0, shuffle_end: int, stats: bool = True, out=None, stream=None):
+    """Monte-Carlo screen (Sec. 3.3): (observed [S, D], totals [S, D, N], McStats or None).
+
+    ``out`` may pass the three output tensors (observed, totals, raw stats or
+    None) to reuse; the launch graph is cached per output address."""
+    lib = _lib.load()
+    a_sets = [_intervals(a, f"a_sets[{i}]") for i, a in enumerate(a_sets)]
+    co = _u32_vec(contig_off, "contig_off")
+    cl = _u32_vec(contig_len, "contig_len")
+    if co.numel() != cl.numel():
+        raise ValueError("contig_off and contig_len differ in length")
+    n_db, n_sets = len(dbs), len(a_sets)
+    nsh = shuffle_end - shuffle_begin
+    if nsh < 0:
+        raise ValueError("shuffle_end < shuffle_begin")
+    dev = a_sets[0].device if a_sets else torch.device("cuda")
+    if out is not None:
+        observed, totals, raw = out
+        if tuple(observed.shape) != (n_sets, n_db) or tuple(totals.shape) != (n_sets, n_db, nsh) \
+                or (raw is not None and tuple(raw.shape) != (n_sets, n_db, 8)):
+            raise ValueError("out tensors have the wrong shapes")
+        for t, nm in ((observed, "observed"), (totals, "totals")):
+            _u64(t, nm)
+        if raw is not None:
+            _u64(raw, "stats")
+    else:
+        observed = torch.empty((n_sets, n_db), dtype=torch.uint64, device=dev)
+        totals = torch.empty((n_sets, n_db, nsh), dtype=torch.uint64, device=dev)
+        raw = torch.empty((n_sets, n_db, 8), dtype=torch.uint64, device=dev) if stats else None
+    hs = (C.c_void_p * max(1, n_db))(*[d._h.value for d in dbs])
+    ps = (C.c_void_p * max(1, n_sets))(*[a.data_ptr() if a.shape[0] else None for a in a_sets])
+    ns = (C.c_uint64 * max(1, n_sets))(*[int(a.shape[0]) for a in a_sets])
+    st = lib.bits_mc_matrix(hs, n_db, ps, ns, n_sets, co.data_ptr(), cl.data_ptr(), co.numel(),
+                            seed, shuffle_begin, shuffle_end,
+                            observed.data_ptr() if observed.numel() else None,
+                            totals.data_ptr() if totals.numel() else None,
+                            raw.data_ptr() if (raw is not None and raw.numel()) else None,
+                            _stream_ptr(stream))
+    _lib.check(st, "bits_mc_matrix")
+    return observed, totals, (McStats(raw) if raw is not None else None)
 
 
 def kernel_launches() -> int:

@@ -20,7 +20,8 @@ METHOD_AUTO, METHOD_SEARCH, METHOD_RMI, METHOD_MERGEPATH = range(4)
 # Every symbol include/bits.h declares.
 EXPORTS = ["bits_build_db", "bits_count", "bits_count_method", "bits_mc", "bits_count_matrix",
            "bits_db_info", "bits_check", "bits_free", "bits_last_error", "bits_kernel_launches",
-           "bits_sort_intervals_noalloc", "bits_db_rmi", "bits_selftest_wait", "bits_project"]
+           "bits_sort_intervals_noalloc", "bits_db_rmi", "bits_selftest_wait", "bits_project",
+           "bits_mc_summary", "bits_mc_matrix", "bits_enumerate_offsets", "bits_enumerate_pairs"]
 
 
 class BitsError(RuntimeError):
@@ -31,7 +32,10 @@ class BitsError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("method", C.c_int32), ("rmi_leaves_log2", C.c_int32),
-                ("top_tree_log2", C.c_int32), ("reserved", C.c_int32)]
+                ("top_tree_log2", C.c_int32), ("flags", C.c_int32)]
+
+
+FLAG_ENUMERATE = 1
 
 
 _lib = None
@@ -60,13 +64,20 @@ def load():
     lib.bits_check.argtypes = [vp, vp]
     lib.bits_sort_intervals_noalloc.argtypes = [u32p, C.c_uint64, u32p, u32p, vp]
     lib.bits_selftest_wait.argtypes = [C.c_uint32, vp]
+    lib.bits_enumerate_offsets.argtypes = [vp, u32p, C.c_uint64, u64p, vp]
+    lib.bits_enumerate_pairs.argtypes = [vp, u32p, C.c_uint64, u64p, u32p, vp]
+    lib.bits_mc_summary.argtypes = [u64p, C.c_uint32, C.c_uint32, u64p, vp, vp]
+    lib.bits_mc_matrix.argtypes = [C.POINTER(C.c_void_p), C.c_uint32, C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_uint64), C.c_uint32, u32p, u32p, C.c_uint32,
+                                   C.c_uint64, C.c_uint32, C.c_uint32, u64p, u64p, vp, vp]
     lib.bits_project.argtypes = [u32p, u32p, u32p, C.c_uint64, u32p, u32p, C.c_uint32, C.c_int32,
                                  u32p, u64p, vp]
     lib.bits_db_rmi.argtypes = [vp, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                 C.POINTER(C.c_float), C.POINTER(C.c_float)]
     for f in ("bits_build_db", "bits_count", "bits_count_method", "bits_mc", "bits_count_matrix",
               "bits_db_info", "bits_check", "bits_sort_intervals_noalloc", "bits_db_rmi",
-              "bits_selftest_wait", "bits_project"):
+              "bits_selftest_wait", "bits_project", "bits_mc_summary", "bits_mc_matrix",
+              "bits_enumerate_offsets", "bits_enumerate_pairs"):
         getattr(lib, f).restype = st
     lib.bits_free.argtypes = [vp]
     lib.bits_free.restype = None

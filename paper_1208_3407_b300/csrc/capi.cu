@@ -15,6 +15,9 @@
 #include "allpairs.cuh"
 #include "mergepath.cuh"
 #include "project.cuh"
+#include "mc_stats.cuh"
+#include "mc_matrix.cuh"
+#include "enumerate.cuh"
 
 namespace bits {
 namespace {
@@ -96,7 +99,8 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   bits_opts o{};
   if (opts) o = *opts;
   const int t = o.top_tree_log2 ? o.top_tree_log2 : 12;
-  if (t < 2 || t > 14 || o.rmi_leaves_log2 < 0 || o.rmi_leaves_log2 > 22 || o.reserved != 0 ||
+  if (t < 2 || t > 14 || o.rmi_leaves_log2 < 0 || o.rmi_leaves_log2 > 22 ||
+      (o.flags & ~BITS_FLAG_ENUMERATE) != 0 ||
       o.method < 0 || o.method > BITS_METHOD_MERGEPATH) {
     set_error("bits_build_db: option out of range");
     return BITS_EINVAL;
@@ -115,7 +119,9 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   db->method = o.method ? o.method : (o.rmi_leaves_log2 ? BITS_METHOD_AUTO : BITS_METHOD_SEARCH);
   db->has_rmi = o.rmi_leaves_log2 > 0;
 
-  // One allocation: bs | be | levels (both arrays) | top images | err | rmi leaves x 2.
+  const bool want_enum = (o.flags & BITS_FLAG_ENUMERATE) != 0;
+  // One allocation: bs | be | levels (both arrays) | top images | err | rmi leaves x 2
+  // | enumeration pairs.
   const size_t n16 = std::max<uint32_t>(round16(nn), 16);
   const size_t off_bs = 0;
   const size_t off_be = align_up(off_bs + sizeof(uint32_t) * n16, 256);
@@ -124,7 +130,8 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   const size_t off_err = align_up(off_top + sizeof(uint32_t) * 2 * db->plan.top_size, 256);
   const size_t off_rmi = align_up(off_err + 256, 256);
   const size_t leaves = db->has_rmi ? (1ull << o.rmi_leaves_log2) : 0;
-  const size_t total = off_rmi + 2 * leaves * sizeof(bits_rmi_leaf);
+  const size_t off_enum = align_up(off_rmi + 2 * leaves * sizeof(bits_rmi_leaf), 256);
+  const size_t total = off_enum + (want_enum ? sizeof(uint2) * std::max<uint32_t>(nn, 1) : 0);
   void* block = nullptr;
   BITS_CUDA_TRY(cudaMalloc(&block, total));
   db->block = block;
@@ -135,6 +142,7 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   db->levels = reinterpret_cast<uint32_t*>(base + off_lv);
   db->top = reinterpret_cast<uint32_t*>(base + off_top);
   db->err = reinterpret_cast<uint32_t*>(base + off_err);
+  if (want_enum) db->enum_e = reinterpret_cast<uint2*>(base + off_enum);
   if (db->has_rmi) {
     db->rmi[0].leaves_log2 = db->rmi[1].leaves_log2 = o.rmi_leaves_log2;
     db->rmi[0].leaves = reinterpret_cast<bits_rmi_leaf*>(base + off_rmi);
@@ -151,7 +159,9 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   if (nn) {
     RadixScratch ws{};
     const size_t sw = radix_status_words(nn);
-    const size_t scratch_bytes = 2 * align_up(sizeof(uint32_t) * nn, 256) +
+    // With enumeration the sort carries indices: 4 more arrays of n words.
+    const size_t words_n = align_up(sizeof(uint32_t) * nn, 256);
+    const size_t scratch_bytes = (want_enum ? 6 : 2) * words_n +
                                  align_up(sizeof(uint32_t) * kRadixHistWords, 256) +
                                  align_up(sizeof(uint32_t) * sw * 8, 256) + 256;
     void* scratch = nullptr;
@@ -167,8 +177,28 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
     ws.status = reinterpret_cast<uint32_t*>(sb);
     sb += align_up(sizeof(uint32_t) * sw * 8, 256);
     ws.tickets = reinterpret_cast<uint32_t*>(sb);
-    bits_status s = radix_sort_intervals(reinterpret_cast<const uint2*>(d_b), nn, db->bs, db->be,
-                                         db->err, ws, st);
+    sb += 256;
+    bits_status s;
+    if (want_enum) {
+      SortSpec spec[2]{};
+      uint32_t* idx_s = reinterpret_cast<uint32_t*>(sb);
+      spec[0].comp = 0;
+      spec[0].out_keys = db->bs;
+      spec[0].tmp_keys = ws.tmp_s;
+      spec[0].out_vals = idx_s;
+      spec[0].tmp_vals = reinterpret_cast<uint32_t*>(sb + words_n);
+      spec[1].comp = 1;
+      spec[1].out_keys = db->be;
+      spec[1].tmp_keys = ws.tmp_e;
+      spec[1].out_vals = reinterpret_cast<uint32_t*>(sb + 2 * words_n);
+      spec[1].tmp_vals = reinterpret_cast<uint32_t*>(sb + 3 * words_n);
+      s = radix_sort_pairs(reinterpret_cast<const uint2*>(d_b), nn, spec, 0, db->err, ws, st,
+                           nullptr);
+      if (s == BITS_OK) s = launch_enum_gather(d_b, idx_s, nn, db->enum_e, st);
+    } else {
+      s = radix_sort_intervals(reinterpret_cast<const uint2*>(d_b), nn, db->bs, db->be, db->err,
+                               ws, st);
+    }
     cudaFreeAsync(scratch, st);
     if (s != BITS_OK) return fail(s);
   }
@@ -286,6 +316,106 @@ bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
                           static_cast<cudaStream_t>(stream));
 }
 
+bits_status bits_enumerate_offsets(const bits_db* db, const uint32_t* d_a, uint64_t n,
+                                   uint64_t* d_offsets, void* stream) {
+  if (!db || !d_offsets || (n && !d_a)) {
+    set_error("bits_enumerate_offsets: NULL argument");
+    return BITS_EINVAL;
+  }
+  if (n >= (1ull << 32)) {
+    set_error("bits_enumerate_offsets: n must be below 2^32");
+    return BITS_EOVERFLOW;
+  }
+  if ((reinterpret_cast<uintptr_t>(d_a) | reinterpret_cast<uintptr_t>(d_offsets)) & 7u) {
+    set_error("bits_enumerate_offsets: pointers must be 8-byte aligned");
+    return BITS_EINVAL;
+  }
+  return run_enumerate_offsets(db, d_a, (uint32_t)n, d_offsets, static_cast<cudaStream_t>(stream));
+}
+
+bits_status bits_enumerate_pairs(const bits_db* db, const uint32_t* d_a, uint64_t n,
+                                 const uint64_t* d_offsets, uint32_t* d_pairs, void* stream) {
+  if (!db || !d_offsets || (n && !d_a)) {
+    set_error("bits_enumerate_pairs: NULL argument");
+    return BITS_EINVAL;
+  }
+  if (!db->enum_e) {
+    set_error("bits_enumerate_pairs: database built without BITS_FLAG_ENUMERATE");
+    return BITS_ENOTIMPL;
+  }
+  if (n >= (1ull << 32)) {
+    set_error("bits_enumerate_pairs: n must be below 2^32");
+    return BITS_EOVERFLOW;
+  }
+  if ((reinterpret_cast<uintptr_t>(d_a) | reinterpret_cast<uintptr_t>(d_offsets) |
+       reinterpret_cast<uintptr_t>(d_pairs)) & 7u) {
+    set_error("bits_enumerate_pairs: pointers must be 8-byte aligned");
+    return BITS_EINVAL;
+  }
+  return run_enumerate_pairs(db, d_a, (uint32_t)n, d_offsets, d_pairs,
+                             static_cast<cudaStream_t>(stream));
+}
+
+bits_status bits_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint32_t* const* d_as,
+                           const uint64_t* n_as, uint32_t n_sets, const uint32_t* d_contig_off,
+                           const uint32_t* d_contig_len, uint32_t n_contigs, uint64_t seed,
+                           uint32_t shuffle_begin, uint32_t shuffle_end, uint64_t* d_observed,
+                           uint64_t* d_totals, bits_mc_stat* d_stats, void* stream) {
+  if ((n_db && !dbs) || (n_sets && (!d_as || !n_as)) || shuffle_end < shuffle_begin) {
+    set_error("bits_mc_matrix: NULL argument or shuffle_end < shuffle_begin");
+    return BITS_EINVAL;
+  }
+  if (n_db == 0 || n_sets == 0) return BITS_OK;
+  if (!d_observed || (shuffle_end > shuffle_begin && !d_totals) || !d_contig_off ||
+      !d_contig_len || n_contigs == 0) {
+    set_error("bits_mc_matrix: NULL output or empty contig table");
+    return BITS_EINVAL;
+  }
+  if (n_contigs > 4096) {
+    set_error("bits_mc_matrix: at most 4096 contigs");
+    return BITS_EOVERFLOW;
+  }
+  if ((reinterpret_cast<uintptr_t>(d_observed) | reinterpret_cast<uintptr_t>(d_totals) |
+       reinterpret_cast<uintptr_t>(d_stats)) & 7u) {
+    set_error("bits_mc_matrix: outputs must be 8-byte aligned");
+    return BITS_EINVAL;
+  }
+  for (uint32_t j = 0; j < n_db; ++j)
+    if (!dbs[j]) {
+      set_error("bits_mc_matrix: NULL database handle");
+      return BITS_EINVAL;
+    }
+  for (uint32_t i = 0; i < n_sets; ++i) {
+    if (n_as[i] >= (1ull << 32)) {
+      set_error("bits_mc_matrix: a query set has 2^32 or more intervals");
+      return BITS_EOVERFLOW;
+    }
+    if (n_as[i] && (!d_as[i] || reinterpret_cast<uintptr_t>(d_as[i]) % 8)) {
+      set_error("bits_mc_matrix: query set pointer NULL or not 8-byte aligned");
+      return BITS_EINVAL;
+    }
+  }
+  return run_mc_matrix(dbs, n_db, d_as, n_as, n_sets, d_contig_off, d_contig_len, n_contigs, seed,
+                       shuffle_begin, shuffle_end, d_observed, d_totals, d_stats,
+                       static_cast<cudaStream_t>(stream));
+}
+
+bits_status bits_mc_summary(const uint64_t* d_totals, uint32_t n_shuffles, uint32_t n_tests,
+                            const uint64_t* d_observed, bits_mc_stat* d_stats, void* stream) {
+  if (n_tests == 0) return BITS_OK;
+  if (!d_observed || !d_stats || (n_shuffles && !d_totals)) {
+    set_error("bits_mc_summary: NULL argument");
+    return BITS_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(d_totals) | reinterpret_cast<uintptr_t>(d_observed) |
+       reinterpret_cast<uintptr_t>(d_stats)) & 7u) {
+    set_error("bits_mc_summary: pointers must be 8-byte aligned");
+    return BITS_EINVAL;
+  }
+  return launch_mc_summary(d_totals, n_shuffles, n_tests, d_observed, d_stats,
+                           static_cast<cudaStream_t>(stream));
+}
+
 bits_status bits_project(const uint32_t* d_contig, const uint32_t* d_start, const uint32_t* d_end,
                          uint64_t n, const uint32_t* d_contig_off, const uint32_t* d_contig_len,
                          uint32_t n_contigs, int32_t closed, uint32_t* d_out,
@@ -361,6 +491,7 @@ void bits_free(bits_db* db) {
   if (prev != db->device) cudaSetDevice(db->device);
   release_mc_graphs(db);
   release_matrix_graphs(db);
+  release_mc_matrix_graphs(db);
   cudaFree(db->block);
   if (prev != db->device) cudaSetDevice(prev);
   delete db;

@@ -56,6 +56,7 @@ struct bits_db {
   int method = BITS_METHOD_SEARCH;
   bool has_rmi = false;
   bits_rmi rmi[2];           // [0] starts, [1] ends
+  uint2* enum_e = nullptr;   // (end, index) in start order, for enumeration (device; optional)
   void* block = nullptr;     // the one device allocation owning all of the above
   size_t block_bytes = 0;
   // Cached MC graphs keyed by the call's arguments.

@@ -7,7 +7,8 @@
 // block of 256 shuffles); a thread owns one shuffle, so the block walks the
 // chunk's intervals out of shared memory (a broadcast read) and keeps its
 // shuffle's running total in a register: one atomic per thread per unit, no
-// reduction tree.  Per placement: one Philox4x32-10 block, a multiply-high
+// reduction tree.  A block of fewer than 256 shuffles splits the chunk's
+// intervals between groups of threads instead (mc_unit.cuh).  Per placement: one Philox4x32-10 block, a multiply-high
 // offset, and the two rank searches of search.cuh (shared-memory top level,
 // then quad-cooperative 64-byte chunks, which for a 1M-interval database all
 // sit in L2).  The interval's contig is found when the chunk is staged.
@@ -18,10 +19,8 @@
 
 #include "count.cuh"
 #include "mc.cuh"
-#include "philox.cuh"
+#include "mc_unit.cuh"
 #include "rmi.cuh"
-#include "rmi_search.cuh"
-#include "search.cuh"
 
 struct bits_mc_graph {
   cudaGraphExec_t exec = nullptr;
@@ -38,10 +37,6 @@ struct bits_mc_graph {
 namespace bits {
 namespace {
 
-constexpr int kMcBlock = 256;    // shuffles per work unit (one per thread)
-constexpr int kMcChunk = 1024;   // intervals per work unit
-constexpr int kMaxContigs = 4096;
-
 struct McArgs {
   const uint2* a;
   uint32_t n;
@@ -54,21 +49,6 @@ struct McArgs {
   uint32_t* err;
   uint32_t nb;
 };
-
-// Contig of a position: last contig whose offset is <= pos, or -1.
-__device__ __forceinline__ int contig_of(const uint32_t* s_coff, uint32_t nc, uint32_t pos) {
-  uint32_t lo = 0, len = nc;  // count of offsets <= pos
-  while (len > 0) {
-    const uint32_t half = len >> 1;
-    if (s_coff[lo + half] <= pos) {
-      lo += half + 1;
-      len -= half + 1;
-    } else {
-      len = half;
-    }
-  }
-  return (int)lo - 1;
-}
 
 template <bool kRmi>
 __global__ void __launch_bounds__(kMcBlock)
@@ -95,42 +75,13 @@ k_mc_search(McArgs P, LevelIndex L, RmiView R) {
     const uint32_t i0 = chunk * kMcChunk;
     const uint32_t cn = min((uint32_t)kMcChunk, P.n - i0);
     __syncthreads();  // previous unit is done with the staged chunk
-    for (uint32_t k = threadIdx.x; k < cn; k += blockDim.x) {
-      const uint2 q = P.a[i0 + k];
-      const int c = contig_of(s_coff, P.nc, q.x);
-      const bool ok = c >= 0 && q.y >= q.x &&
-                      (unsigned long long)q.y <= (unsigned long long)s_coff[c] + s_clen[c];
-      if (ok) {
-        s_off[k] = s_coff[c];
-        s_len[k] = q.y - q.x;
-        s_rng[k] = s_clen[c] - (q.y - q.x) + 1u;
-      } else {
-        bad = true;
-        s_off[k] = q.x;
-        s_len[k] = 0u;
-        s_rng[k] = 1u;
-      }
-    }
+    mc_stage_chunk(P.a, i0, cn, s_coff, s_clen, P.nc, s_off, s_len, s_rng, bad);
     __syncthreads();
-    const uint32_t s_local = sb * kMcBlock + threadIdx.x;
-    const uint32_t s = P.s_begin + s_local;
-    unsigned long long acc = 0ull;
-    for (uint32_t k = 0; k < cn; ++k) {
-      const uint32_t off = s_off[k], rng = s_rng[k], len = s_len[k];
-      const uint4 x = philox4x32_10(make_uint4(i0 + k, s, 0u, 0u), P.key0, P.key1);
-      const uint32_t start = off + philox_offset(x, rng);
-      const uint32_t end = start + len;
-      uint32_t rs, re;
-      const uint32_t key_s = end, key_e = start + 1u;
-      if (kRmi) {
-        rmi_rank2(R, L, P.nb, key_s, key_e, rs, re, false);
-      } else {
-        top_rank2(s_top, L.top_size, key_s, key_e, rs, re);
-        quad_descend(L, rs, key_s, re, key_e, false);
-      }
-      acc += icount_from_ranks(rs, re, start, P.nb);
-    }
-    if (s_local < P.n_shuffles && acc) atomicAdd(P.totals + s_local, acc);
+    const McLane ln = mc_lane(sb, P.n_shuffles);
+    const unsigned long long acc = mc_count_chunk<kRmi>(s_top, L, R, P.nb, s_off, s_len, s_rng, i0,
+                                                        cn, ln, P.s_begin + ln.s_local, 0u, P.key0,
+                                                        P.key1);
+    if (ln.active && acc) atomicAdd(P.totals + ln.s_local, acc);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_dev_error(P.err, DEV_ERR_INVALID);
 }

@@ -6,8 +6,11 @@ Workloads (inputs from the seeded generator ``bits_synth``):
     count-200k-20m   bits_count, 200,000 queries vs 20,000,000 reads (exome-vs-reads)
     count-100m-100m  bits_count, 100M queries vs 100M intervals (learned index built)
     build-20m        bits_build_db of the 20,000,000 reads
+    enumerate-200k-20m  every intersecting pair of those queries and reads
     mc-100k-1m       bits_mc, 100,000 intervals vs 1,000,000, 10,000 shuffles
     allpairs-64x32   bits_count_matrix, 64 query sets x 32 databases
+    mc-screen-64x32  bits_mc_matrix over those sets, 4 shuffles, with the summary
+    mc-screen-16x8   the same on the first 16 query sets and 8 databases
 
 Every call checks the device error word at the end; the script prints one
 line per workload with the device time of the last repetition.
@@ -25,7 +28,8 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 import bits_synth  # noqa: E402
 
-from . import METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, Database, count_matrix  # noqa: E402
+from . import (METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, Database, count_matrix,  # noqa: E402
+               mc_matrix)
 
 METHODS = {"search": METHOD_SEARCH, "rmi": METHOD_RMI, "mergepath": METHOD_MERGEPATH}
 
@@ -63,6 +67,13 @@ def main(argv=None):
         for _ in range(args.reps):
             ms = _timed(lambda: db.count(a, counts=counts, total=total, method=m, check=False))
         db.check()
+    elif args.name == "enumerate-200k-20m":
+        _, a_np, b_np = bits_synth.config2()
+        db = Database(_dev(b_np), enumerate=True)
+        a = _dev(a_np)
+        for _ in range(args.reps):
+            ms = _timed(lambda: db.enumerate(a, check=False))
+        db.check()
     elif args.name == "build-20m":
         _, _, b_np = bits_synth.config2()
         b = _dev(b_np)
@@ -86,6 +97,21 @@ def main(argv=None):
         out = torch.empty((len(a), len(dbs)), dtype=torch.uint64, device="cuda")
         for _ in range(args.reps):
             ms = _timed(lambda: count_matrix(dbs, a, out=out))
+        for d in dbs:
+            d.check()
+    elif args.name in ("mc-screen-64x32", "mc-screen-16x8"):
+        genome, a_sets, b_sets = bits_synth.config5()
+        if args.name == "mc-screen-16x8":
+            a_sets, b_sets = a_sets[:16], b_sets[:8]
+        co, cl = bits_synth.mc_contig_table(genome)
+        dbs = [Database(_dev(b)) for b in b_sets]
+        a = [_dev(x) for x in a_sets]
+        dco, dcl = _dev(co), _dev(cl)
+        out = (torch.empty((len(a), len(dbs)), dtype=torch.uint64, device="cuda"),
+               torch.empty((len(a), len(dbs), 4), dtype=torch.uint64, device="cuda"),
+               torch.empty((len(a), len(dbs), 8), dtype=torch.uint64, device="cuda"))
+        for _ in range(args.reps):
+            ms = _timed(lambda: mc_matrix(dbs, a, dco, dcl, seed=17, shuffle_end=4, out=out))
         for d in dbs:
             d.check()
     else:
