@@ -2,6 +2,7 @@
 // database construction and ownership, argument checking, method dispatch,
 // error reporting and the launch counter.
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -44,6 +45,23 @@ int sm_count() {
     g_sm_count[dev] = v > 0 ? v : 1;
   }
   return g_sm_count[dev];
+}
+
+int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap) {
+  int dev = 0, per_sm_smem = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, smem);
+  b = std::max(1, std::min(b, cap));
+  if (per_sm_smem > 0) {
+    const double need = (double)b * (double)(smem + (size_t)reserved);
+    const int pct = std::min(100, (int)std::ceil(100.0 * need / per_sm_smem));
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  }
+  return b;
 }
 
 bits_status cuda_status(cudaError_t e, const char* what) {

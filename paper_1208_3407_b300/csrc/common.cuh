@@ -28,6 +28,11 @@ void set_error(const std::string& msg);
 void count_launch(uint32_t k = 1);
 void uncount_launch(uint64_t k);
 int sm_count();
+// Resident CTAs per SM for a kernel with `smem` bytes of dynamic shared
+// memory, capped at `cap`, with the shared-memory carveout set to what that
+// many CTAs need so the rest of the SM's on-chip memory stays L1 (defined in
+// capi.cu).
+int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap);
 bits_status cuda_status(cudaError_t e, const char* what);
 
 #define BITS_CUDA_TRY(expr)                                         \

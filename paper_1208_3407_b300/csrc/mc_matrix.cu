@@ -123,10 +123,8 @@ int mcm_blocks_per_sm(size_t smem) {
   static int per_sm = 0;
   static size_t smem_for = 0;
   if (per_sm == 0 || smem_for != smem) {
-    cudaFuncSetAttribute(k_mc_matrix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mc_matrix, kMcBlock, smem);
-    per_sm = std::max(1, b);
+    per_sm = occupancy_with_l1(reinterpret_cast<const void*>(k_mc_matrix), kMcBlock, smem,
+                               kMcCtasPerSm);
     smem_for = smem;
   }
   return per_sm;

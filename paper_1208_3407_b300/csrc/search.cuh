@@ -67,43 +67,52 @@ __device__ __forceinline__ uint32_t cnt4(const uint4 v, uint32_t key) {
          (uint32_t)(v.w < key);
 }
 
-// Shared-memory layout of the top level.  A power-of-two search probes index
-// pos + step - 1, which for step >= 32 is the same index mod 32 in every
-// lane: all 32 lanes would hit one bank.  One pad word after every 32
-// entries sends those probes to different banks.
-__device__ __forceinline__ uint32_t top_slot(uint32_t i) { return i + (i >> 5); }
-__host__ __device__ __forceinline__ uint32_t top_words(uint32_t size) { return size + (size >> 5); }
+// Shared-memory layout of the top level: each array's image (size = 2^h
+// entries, sorted, the last one always padding) is stored in Eytzinger
+// (breadth-first) order, node k (1 <= k < size) at index k, so that a search
+// is h steps of k = 2k + (node < key): one shared load, one compare and one
+// shift-add per step, and the final k - size is the rank.  Node k at depth d
+// holds sorted entry ((2 (k - 2^d) + 1) << (h - 1 - d)) - 1; index 0 is
+// unused.  `size` words per array.
+__host__ __device__ __forceinline__ uint32_t top_words(uint32_t size) { return size; }
 
-// #(s[0 .. size-1) < key) for a power-of-two size whose tail is padded with
-// 0xFFFFFFFF; two independent searches in lock step.  s_top holds the start
-// array then the end array, each in the padded layout of top_slot.
+// #(s[0 .. size-1) < key) for both arrays' tops (starts, then ends), two
+// independent searches in lock step.
 __device__ __forceinline__ void top_rank2(const uint32_t* __restrict__ s_top, uint32_t size,
                                           uint32_t key_s, uint32_t key_e, uint32_t& is,
                                           uint32_t& ie) {
-  const uint32_t* s_e = s_top + top_words(size);
-  uint32_t ps = 0u, pe = 0u;
+  const uint32_t* s_e = s_top + size;
+  uint32_t ks = 1u, ke = 1u;
   for (uint32_t step = size >> 1; step; step >>= 1) {
-    if (s_top[top_slot(ps + step - 1u)] < key_s) ps += step;
-    if (s_e[top_slot(pe + step - 1u)] < key_e) pe += step;
+    ks = 2u * ks + (s_top[ks] < key_s ? 1u : 0u);
+    ke = 2u * ke + (s_e[ke] < key_e ? 1u : 0u);
   }
-  is = ps;
-  ie = pe;
+  is = ks - size;
+  ie = ke - size;
 }
 
-// Cooperative copy of the two top-level images into shared memory, padded.
+// Cooperative copy of the two sorted top images into shared memory in
+// Eytzinger order: coalesced 16-byte reads, scattered shared-memory writes.
+// Sorted entry p (< size - 1) goes to node (1 << (h - 1 - t)) + ((p + 1) >> (t + 1)),
+// t = trailing zeros of p + 1; entry size - 1 (padding) has no node.
 __device__ __forceinline__ void load_top(uint32_t* s_top, const LevelIndex& L) {
   const uint4* src = reinterpret_cast<const uint4*>(L.top);
-  const uint32_t size = L.top_size, words = top_words(size);
+  const uint32_t size = L.top_size;
+  const int h = 31 - __clz(size);
   for (uint32_t i = threadIdx.x; i < (2u * size) / 4u; i += blockDim.x) {
     const uint4 v = src[i];
-    const uint32_t e = 4u * i;                       // element index over both arrays
-    const uint32_t a = e >= size ? 1u : 0u;          // which array
-    uint32_t* dst = s_top + a * words + top_slot(e - a * size);  // 4 | 32, so one pad run
-    dst[0] = v.x;
-    dst[1] = v.y;
-    dst[2] = v.z;
-    dst[3] = v.w;
+    const uint32_t e = 4u * i;                 // element index over both arrays
+    const uint32_t a = e >= size ? 1u : 0u;    // which array (4 | size: one array per uint4)
+    uint32_t* dst = s_top + a * size;
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t p1 = e - a * size + (uint32_t)q + 1u;  // sorted position + 1
+      const int t = __ffs(p1) - 1;
+      if (t < h) dst[(1u << (h - 1 - t)) + (p1 >> (t + 1))] = w[q];
+    }
   }
+  if (threadIdx.x < 2) s_top[threadIdx.x * size] = kU32Max;  // unused node 0
 }
 
 // Descend the 16-ary levels for the two searches (starts, ends) of every
