@@ -58,6 +58,33 @@ def test_host_side_argument_checks(lib):
     assert lib.bits_mc(None, 0, None, 0, None, None, 0, 0, 0, 0, None, None, None, None,
                        None) == _lib.BITS_EINVAL
     assert lib.bits_count_matrix(None, 1, None, None, 0, None, None) == _lib.BITS_EINVAL
+    unknown_flag = _lib.Opts(0, 0, 0, 2)
+    assert lib.bits_build_db(C.c_void_p(256), 4, C.byref(unknown_flag), None,
+                             C.byref(h)) == _lib.BITS_EINVAL
+    # projection: size, mode and pointer checks
+    assert lib.bits_project(None, None, None, 1 << 32, None, None, 0, 0, None, None,
+                            None) == _lib.BITS_EOVERFLOW
+    assert lib.bits_project(None, None, None, 0, None, None, 0, 2, None, None,
+                            None) == _lib.BITS_EINVAL
+    assert lib.bits_project(None, None, None, 3, None, None, 0, 0, None, None,
+                            None) == _lib.BITS_EINVAL
+    assert lib.bits_project(None, C.c_void_p(256), C.c_void_p(512), 3, None, None, 2, 0,
+                            C.c_void_p(1024), None, None) == _lib.BITS_EINVAL   # ids missing
+    assert lib.bits_project(None, None, None, 0, None, None, 0, 1, None, None, None) == _lib.BITS_OK
+    # Monte-Carlo summary and screen
+    assert lib.bits_mc_summary(None, 10, 0, None, None, None) == _lib.BITS_OK
+    assert lib.bits_mc_summary(None, 10, 2, None, None, None) == _lib.BITS_EINVAL
+    assert lib.bits_mc_summary(C.c_void_p(260), 10, 2, C.c_void_p(256), C.c_void_p(512),
+                               None) == _lib.BITS_EINVAL                       # misaligned
+    assert lib.bits_mc_matrix(None, 1, None, None, 1, None, None, 0, 0, 0, 0, None, None, None,
+                              None) == _lib.BITS_EINVAL
+    assert lib.bits_mc_matrix(None, 0, None, None, 0, None, None, 0, 0, 5, 4, None, None, None,
+                              None) == _lib.BITS_EINVAL                       # end < begin
+    assert lib.bits_mc_matrix(None, 0, None, None, 0, None, None, 0, 0, 0, 4, None, None, None,
+                              None) == _lib.BITS_OK                           # nothing to do
+    # enumeration
+    assert lib.bits_enumerate_offsets(None, None, 0, None, None) == _lib.BITS_EINVAL
+    assert lib.bits_enumerate_pairs(None, None, 0, None, None, None) == _lib.BITS_EINVAL
     lib.bits_free(None)
     assert lib.bits_kernel_launches() == 0
 
