@@ -102,6 +102,34 @@ bits_status bits_count_method(const bits_db* db, int32_t method, const uint32_t*
                               uint64_t n, uint32_t* d_counts, uint64_t* d_total, void* stream);
 
 /*
+ * bits_count_host -- bits_count_method on host buffers: the queries come
+ * from host memory and the counts and the total go back to it within the
+ * one call (Algorithm 2 over Algorithm 1, as bits_count).
+ *   method    a bits_method; AUTO takes the choice the autotuner made for
+ *             this size class (plain search until one has been tuned).
+ *   h_a       host, n queries as (start, end) uint32 pairs, 8-byte aligned.
+ *   n         number of queries, n < 2^32.
+ *   h_counts  host uint32[n] receiving ICount(a_i), 4-byte aligned, or NULL.
+ *   h_total   host uint64 receiving the sum over all queries, 8-byte aligned.
+ * Page-locked buffers (cudaHostAlloc, cudaMallocHost, cudaHostRegister; the
+ * whole range inside one such allocation) are read and written in place by
+ * the search kernel over the bus, so the transfers overlap the searches and
+ * nothing is staged.  Pageable buffers are staged through stream-ordered
+ * device memory with cudaMemcpyAsync; merge path always stages.  The total
+ * is added up in a stream-ordered device word of the call's own and copied
+ * to h_total.  That memory comes from a pool the library creates per device
+ * at the first call and keeps (up to 64 MiB reserved) for the process.  Stream-ordered like every call: with
+ * page-locked buffers it returns at once and the results are in place when
+ * `stream` has been synchronised; a pageable h_total or h_counts makes the
+ * call wait for its copy, as cudaMemcpyAsync does.  Inverted queries count
+ * 0 and set the database's device error word (bits_check).  BITS_EINVAL if a
+ * buffer is device memory or the database belongs to another device than
+ * the current one.
+ */
+bits_status bits_count_host(const bits_db* db, int32_t method, const uint32_t* h_a, uint64_t n,
+                            uint32_t* h_counts, uint64_t* h_total, void* stream);
+
+/*
  * Enumeration problem (Sec. 1.1: report every intersecting pair), in two
  * stream-ordered steps so that the caller can size the output in between.
  *

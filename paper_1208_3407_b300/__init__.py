@@ -126,6 +126,55 @@ class Database:
             _lib.check(self._lib.bits_check(self._h, sp), "bits_count (device check)")
         return out, total
 
+    def count_host(self, a, *, counts=True, total: torch.Tensor | None = None,
+                   method: int = METHOD_AUTO, stream=None, check: bool = True):
+        """bits_count_host: queries in host memory, counts and total back in it.
+
+        ``a`` is a CPU tensor or numpy array of shape ``(n, 2)`` (uint32 or
+        int32, C-contiguous).  ``counts`` is True (a new host array: page-
+        locked when ``a`` is), False/None (total only) or a CPU uint32/int32
+        tensor or numpy array of >= n elements that receives them.  ``total``
+        is None (the total is returned as an int, which waits for it) or a
+        page-locked uint64 CPU tensor of one element that receives it.
+        Page-locked buffers are read and written in place by the search
+        kernel; pageable ones are staged through device memory by the
+        library.  With ``check`` the stream is synchronised and the device
+        error word read (inverted queries raise); without it and with
+        page-locked buffers the call is asynchronous and the results are in
+        place once the stream has been synchronised.
+        Returns ``(counts or None, total)``."""
+        a_t = torch.from_numpy(a) if not isinstance(a, torch.Tensor) else a
+        if a_t.is_cuda or a_t.dtype not in _U32 or a_t.dim() != 2 or a_t.shape[1] != 2:
+            raise TypeError("a must be a host (n, 2) uint32/int32 array")
+        if not a_t.is_contiguous():
+            raise ValueError("a must be contiguous")
+        n = int(a_t.shape[0])
+        if counts is True:
+            out = torch.empty(n, dtype=torch.uint32, pin_memory=bool(n) and a_t.is_pinned())
+        elif counts is None or counts is False:
+            out = None
+        else:
+            out = torch.from_numpy(counts) if not isinstance(counts, torch.Tensor) else counts
+            if (out.is_cuda or out.dtype not in _U32 or out.numel() < n
+                    or not out.is_contiguous()):
+                raise TypeError("counts must be a contiguous host uint32 array of >= n elements")
+        if total is None:
+            tot = C.c_uint64()
+            tp = C.addressof(tot)
+        else:
+            if total.is_cuda or total.dtype != torch.uint64 or total.numel() < 1:
+                raise TypeError("total must be a host uint64 tensor of >= 1 element")
+            tp = total.data_ptr()
+        sp = _stream_ptr(stream)
+        with torch.cuda.device(self.device):
+            st = self._lib.bits_count_host(self._h, method, a_t.data_ptr() if n else None, n,
+                                           out.data_ptr() if (out is not None and n) else None,
+                                           tp, sp)
+            _lib.check(st, "bits_count_host")
+            if check:
+                _lib.check(self._lib.bits_check(self._h, sp), "bits_count_host (device check)")
+        return out, (tot.value if total is None else total)
+
     def enumerate(self, a: torch.Tensor, *, stream=None, check: bool = True):
         """Every intersecting pair (Sec. 1.1's enumeration problem).
 

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "BITS_OK", 1: "BITS_EINVAL", 2: "BITS_ENOMEM", 3: "BITS_ECUDA
 METHOD_AUTO, METHOD_SEARCH, METHOD_RMI, METHOD_MERGEPATH = range(4)
 
 # Every symbol include/bits.h declares.
-EXPORTS = ["bits_build_db", "bits_count", "bits_count_method", "bits_mc", "bits_count_matrix",
+EXPORTS = ["bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc", "bits_count_matrix",
            "bits_db_info", "bits_check", "bits_free", "bits_last_error", "bits_kernel_launches",
            "bits_sort_intervals_noalloc", "bits_db_rmi", "bits_selftest_wait", "bits_project",
            "bits_mc_summary", "bits_mc_matrix", "bits_enumerate_offsets", "bits_enumerate_pairs"]
@@ -54,6 +54,7 @@ def load():
     lib.bits_build_db.argtypes = [u32p, C.c_uint64, C.POINTER(Opts), vp, C.POINTER(C.c_void_p)]
     lib.bits_count.argtypes = [vp, u32p, C.c_uint64, u32p, u64p, vp]
     lib.bits_count_method.argtypes = [vp, C.c_int32, u32p, C.c_uint64, u32p, u64p, vp]
+    lib.bits_count_host.argtypes = [vp, C.c_int32, vp, C.c_uint64, vp, vp, vp]
     lib.bits_mc.argtypes = [vp, C.c_int32, u32p, C.c_uint64, u32p, u32p, C.c_uint32, C.c_uint64,
                             C.c_uint32, C.c_uint32, u64p, C.POINTER(C.c_uint64),
                             C.POINTER(C.c_uint64), C.POINTER(C.c_double), vp]
@@ -74,8 +75,8 @@ def load():
                                  u32p, u64p, vp]
     lib.bits_db_rmi.argtypes = [vp, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                 C.POINTER(C.c_float), C.POINTER(C.c_float)]
-    for f in ("bits_build_db", "bits_count", "bits_count_method", "bits_mc", "bits_count_matrix",
-              "bits_db_info", "bits_check", "bits_sort_intervals_noalloc", "bits_db_rmi",
+    for f in ("bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc",
+              "bits_count_matrix", "bits_db_info", "bits_check", "bits_sort_intervals_noalloc", "bits_db_rmi",
               "bits_selftest_wait", "bits_project", "bits_mc_summary", "bits_mc_matrix",
               "bits_enumerate_offsets", "bits_enumerate_pairs"):
         getattr(lib, f).restype = st

@@ -48,6 +48,26 @@ bits_status cuda_status(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::bits::cuda_status(_e, what);    \
   } while (0)
 
+// Launch configuration of a programmatic dependent launch: the kernel may
+// start while the kernel before it in the stream drains, and must execute
+// griddepcontrol.wait before it touches what that kernel writes.
+inline void pdl_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, dim3 grid, dim3 block,
+                       size_t smem, cudaStream_t st) {
+  cfg = cudaLaunchConfig_t{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+}
+
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ void set_dev_error(uint32_t* err, uint32_t bit) {
   if (err) atomicOr(err, bit);
 }

@@ -16,20 +16,30 @@ namespace {
 
 constexpr int kCountBlock = 512;
 
+// Zeroes the total that k_count_search accumulates into, then lets the
+// count kernel, launched right behind it as a programmatic dependent, start
+// at once: the count kernel stages its top level and runs its searches while
+// this grid drains, and waits for it (griddepcontrol.wait) only before its
+// one atomic on the total.
+__global__ void k_zero_total(unsigned long long* __restrict__ total) {
+  if (threadIdx.x == 0) *total = 0ull;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(kCountBlock, 2)
 k_count_search(const uint2* __restrict__ a, uint32_t n, LevelIndex L, uint32_t nb,
                uint32_t* __restrict__ counts, unsigned long long* __restrict__ total,
                uint32_t* __restrict__ err) {
   extern __shared__ __align__(16) uint32_t s_top[];
   __shared__ unsigned long long s_red[32];
+  const uint32_t stride = gridDim.x * blockDim.x;
   load_top(s_top, L);
   __syncthreads();
-
   unsigned long long acc = 0ull;
   bool bad = false;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
-    const uint32_t i = base + threadIdx.x;
+  // 64-bit indices: n may come within one grid stride of 2^32.
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const uint64_t i = base + threadIdx.x;
     const bool valid = i < n;
     uint2 q = make_uint2(0u, 0u);
     if (valid) q = __ldcs(a + i);
@@ -49,6 +59,7 @@ k_count_search(const uint2* __restrict__ a, uint32_t n, LevelIndex L, uint32_t n
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_dev_error(err, DEV_ERR_INVALID);
   const unsigned long long sum = block_sum_u64(acc, s_red);
+  grid_dependency_wait();
   if (threadIdx.x == 0 && sum) atomicAdd(total, sum);
 }
 
@@ -149,17 +160,25 @@ bits_status build_levels(bits_db* db, cudaStream_t st) {
   return BITS_OK;
 }
 
+bits_status launch_zero_total(uint64_t* d_total, cudaStream_t st) {
+  k_zero_total<<<1, 32, 0, st>>>(reinterpret_cast<unsigned long long*>(d_total));
+  BITS_LAUNCH_CHECK("k_zero_total");
+  return BITS_OK;
+}
+
 bits_status launch_count_search(const bits_db* db, const uint32_t* d_a, uint32_t n,
                                 uint32_t* d_counts, uint64_t* d_total, cudaStream_t st) {
-  BITS_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), st));
-  if (n == 0) return BITS_OK;
+  bits_status s = launch_zero_total(d_total, st);
+  if (s != BITS_OK || n == 0) return s;
   const size_t smem = sizeof(uint32_t) * 2 * top_words(db->lvl.top_size);
   const uint32_t need = (n + kCountBlock - 1) / kCountBlock;
   const uint32_t grid = std::min<uint32_t>(need, (uint32_t)(count_blocks_per_sm(smem) * sm_count()));
-  k_count_search<<<grid, kCountBlock, smem, st>>>(reinterpret_cast<const uint2*>(d_a), n, db->lvl,
-                                                  db->n, d_counts,
-                                                  reinterpret_cast<unsigned long long*>(d_total),
-                                                  db->err);
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  pdl_config(cfg, attr, dim3(grid), dim3(kCountBlock), smem, st);
+  BITS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_count_search, reinterpret_cast<const uint2*>(d_a), n,
+                                   db->lvl, db->n, d_counts,
+                                   reinterpret_cast<unsigned long long*>(d_total), db->err));
   BITS_LAUNCH_CHECK("k_count_search");
   return BITS_OK;
 }

@@ -16,7 +16,13 @@ void plan_levels(uint32_t n, int top_log2, LevelPlan& p);
 // padding from the sorted arrays db->bs / db->be.
 bits_status build_levels(bits_db* db, cudaStream_t st);
 
-// Plain BITS count through the 16-ary levels.  Zeroes *d_total, then
+// Zero a count's 64-bit total with a one-CTA kernel that immediately lets a
+// programmatic dependent launched behind it start; that kernel waits for it
+// (grid_dependency_wait) before adding to the total.
+bits_status launch_zero_total(uint64_t* d_total, cudaStream_t st);
+
+// Plain BITS count through the 16-ary levels.  Zeroes *d_total (a one-CTA
+// kernel the count kernel overlaps as a programmatic dependent), then
 // accumulates; d_counts may be NULL.
 bits_status launch_count_search(const bits_db* db, const uint32_t* d_a, uint32_t n,
                                 uint32_t* d_counts, uint64_t* d_total, cudaStream_t st);

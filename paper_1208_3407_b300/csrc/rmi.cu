@@ -194,6 +194,7 @@ k_count_rmi(const uint2* __restrict__ a, uint32_t n, LevelIndex L, RmiView R, ui
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_dev_error(err, DEV_ERR_INVALID);
   const unsigned long long sum = block_sum_u64(acc, s_red);
+  grid_dependency_wait();  // the total was zeroed by the kernel before this one
   if (threadIdx.x == 0 && sum) atomicAdd(total, sum);
 }
 
@@ -286,14 +287,16 @@ bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t
 
 bits_status launch_count_rmi(const bits_db* db, const uint32_t* d_a, uint32_t n,
                              uint32_t* d_counts, uint64_t* d_total, cudaStream_t st) {
-  BITS_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), st));
-  if (n == 0) return BITS_OK;
+  bits_status s = launch_zero_total(d_total, st);
+  if (s != BITS_OK || n == 0) return s;
   const uint32_t need = (n + kCountBlock - 1) / kCountBlock;
   const uint32_t grid = std::min<uint32_t>(need, (uint32_t)(rmi_count_blocks_per_sm() * sm_count()));
-  k_count_rmi<<<grid, kCountBlock, 0, st>>>(reinterpret_cast<const uint2*>(d_a), n, db->lvl,
-                                            rmi_view(db), db->n, d_counts,
-                                            reinterpret_cast<unsigned long long*>(d_total),
-                                            db->err);
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  pdl_config(cfg, attr, dim3(grid), dim3(kCountBlock), 0, st);
+  BITS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_count_rmi, reinterpret_cast<const uint2*>(d_a), n,
+                                   db->lvl, rmi_view(db), db->n, d_counts,
+                                   reinterpret_cast<unsigned long long*>(d_total), db->err));
   BITS_LAUNCH_CHECK("k_count_rmi");
   return BITS_OK;
 }

@@ -53,6 +53,7 @@ def test_host_side_argument_checks(lib):
     assert lib.bits_build_db(C.c_void_p(256), 4, C.byref(rmi_without_leaves), None,
                              C.byref(h)) == _lib.BITS_EINVAL
     assert lib.bits_count(None, None, 0, None, None, None) == _lib.BITS_EINVAL
+    assert lib.bits_count_host(None, 1, None, 0, None, None, None) == _lib.BITS_EINVAL
     assert lib.bits_check(None, None) == _lib.BITS_EINVAL
     assert lib.bits_db_info(None, None, None, None, None) == _lib.BITS_EINVAL
     assert lib.bits_mc(None, 0, None, 0, None, None, 0, 0, 0, 0, None, None, None, None,
