@@ -314,6 +314,25 @@ bits_status bits_sort_intervals_noalloc(const uint32_t* d_b, uint64_t n, uint32_
  */
 bits_status bits_selftest_wait(uint32_t spin_limit, void* stream);
 
+/*
+ * bits_probe_random_reads -- diagnostic (not in the paper): the rate at
+ * which this GPU serves random 64-byte node reads, the access every search
+ * kernel makes once per tree level; on a database much larger than L2 the
+ * level-0 reads come from DRAM and this rate bounds the counting kernels.
+ * Quads of lanes read uniformly random 64-byte nodes of d_buf with a 64-byte
+ * line fill, four nodes in flight per quad, timed with CUDA events.
+ *   d_buf          device buffer, 64-byte aligned, `bytes` long (contents
+ *                  are read, not used); much larger than L2 (e.g. 4 GiB) for
+ *                  the DRAM rate.
+ *   bytes          a multiple of 64, at most 64 * (2^32 - 1).
+ *   n_reads        node reads to issue, 1 .. 2^34 (rounded up to whole
+ *                  rounds of the grid).
+ *   h_nodes_per_s  host double receiving the node reads per second.
+ * Synchronises `stream`.
+ */
+bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes, uint64_t n_reads,
+                                    double* h_nodes_per_s, void* stream);
+
 /* Read-only views of the database (sorted starts, sorted ends, size). */
 bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_t** d_be,
                          uint64_t* n, int32_t* has_rmi);

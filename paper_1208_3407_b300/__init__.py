@@ -20,7 +20,7 @@ from ._lib import (METHOD_AUTO, METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, Bit
                    LIB_PATH)
 
 __all__ = ["Database", "count_matrix", "project", "mc_summary", "mc_matrix", "McStats",
-           "kernel_launches", "BitsError", "METHOD_AUTO",
+           "kernel_launches", "probe_random_reads", "BitsError", "METHOD_AUTO",
            "METHOD_SEARCH", "METHOD_RMI", "METHOD_MERGEPATH", "LIB_PATH", "device_view"]
 
 _U32 = (torch.uint32, torch.int32)
@@ -396,6 +396,21 @@ def mc_matrix(dbs, a_sets, contig_off: torch.Tensor, contig_len: torch.Tensor, *
                             _stream_ptr(stream))
     _lib.check(st, "bits_mc_matrix")
     return observed, totals, (McStats(raw) if raw is not None else None)
+
+
+def probe_random_reads(nbytes: int = 4 << 30, n_reads: int = 1 << 24, *, device=None,
+                       stream=None) -> float:
+    """bits_probe_random_reads on a fresh ``nbytes`` device buffer: random
+    64-byte node reads per second (the bound of the search kernels on a
+    database much larger than L2)."""
+    buf = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+    rate = C.c_double()
+    with torch.cuda.device(buf.device):
+        _lib.check(_lib.load().bits_probe_random_reads(buf.data_ptr(), nbytes, n_reads,
+                                                       C.byref(rate), _stream_ptr(stream)),
+                   "bits_probe_random_reads")
+    del buf
+    return rate.value
 
 
 def kernel_launches() -> int:

@@ -18,10 +18,11 @@ STATUS_NAMES = {0: "BITS_OK", 1: "BITS_EINVAL", 2: "BITS_ENOMEM", 3: "BITS_ECUDA
 METHOD_AUTO, METHOD_SEARCH, METHOD_RMI, METHOD_MERGEPATH = range(4)
 
 # Every symbol include/bits.h declares.
-EXPORTS = ["bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc", "bits_count_matrix",
-           "bits_db_info", "bits_check", "bits_free", "bits_last_error", "bits_kernel_launches",
+EXPORTS = ["bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc",
+           "bits_count_matrix", "bits_db_info", "bits_check", "bits_free", "bits_last_error", "bits_kernel_launches",
            "bits_sort_intervals_noalloc", "bits_db_rmi", "bits_selftest_wait", "bits_project",
-           "bits_mc_summary", "bits_mc_matrix", "bits_enumerate_offsets", "bits_enumerate_pairs"]
+           "bits_mc_summary", "bits_mc_matrix", "bits_enumerate_offsets", "bits_enumerate_pairs",
+           "bits_probe_random_reads"]
 
 
 class BitsError(RuntimeError):
@@ -65,6 +66,7 @@ def load():
     lib.bits_check.argtypes = [vp, vp]
     lib.bits_sort_intervals_noalloc.argtypes = [u32p, C.c_uint64, u32p, u32p, vp]
     lib.bits_selftest_wait.argtypes = [C.c_uint32, vp]
+    lib.bits_probe_random_reads.argtypes = [vp, C.c_uint64, C.c_uint64, C.POINTER(C.c_double), vp]
     lib.bits_enumerate_offsets.argtypes = [vp, u32p, C.c_uint64, u64p, vp]
     lib.bits_enumerate_pairs.argtypes = [vp, u32p, C.c_uint64, u64p, u32p, vp]
     lib.bits_mc_summary.argtypes = [u64p, C.c_uint32, C.c_uint32, u64p, vp, vp]
@@ -78,7 +80,7 @@ def load():
     for f in ("bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc",
               "bits_count_matrix", "bits_db_info", "bits_check", "bits_sort_intervals_noalloc", "bits_db_rmi",
               "bits_selftest_wait", "bits_project", "bits_mc_summary", "bits_mc_matrix",
-              "bits_enumerate_offsets", "bits_enumerate_pairs"):
+              "bits_enumerate_offsets", "bits_enumerate_pairs", "bits_probe_random_reads"):
         getattr(lib, f).restype = st
     lib.bits_free.argtypes = [vp]
     lib.bits_free.restype = None

@@ -1,0 +1,104 @@
+// bits_probe_random_reads: the rate at which this GPU serves random 64-byte
+// node reads from DRAM.
+//
+// Every search kernel here reads one 64-byte node per level of the 16-ary
+// tree, loaded by a quad of lanes (16 bytes each) with a 64-byte line fill.
+// On a database much larger than L2 the level-0 nodes come from DRAM at
+// random, and the rate of such reads, not the byte bandwidth, bounds the
+// kernels: random 64-byte reads reach about a third of the copy bandwidth.
+// This probe issues exactly that access -- quads reading uniformly random
+// nodes of a buffer, four independent nodes in flight per quad -- and times
+// it with CUDA events, so the search kernels can be set against the same
+// hardware limit.
+#include "common.cuh"
+
+namespace bits {
+namespace {
+
+constexpr int kProbeBlock = 512;
+constexpr int kProbeInFlight = 4;
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  // Murmur3's 32-bit finaliser: spreads the node index over the buffer.
+  x ^= x >> 16;
+  x *= 0x85EBCA6Bu;
+  x ^= x >> 13;
+  x *= 0xC2B2AE35u;
+  x ^= x >> 16;
+  return x;
+}
+
+__global__ void __launch_bounds__(kProbeBlock)
+k_probe_random(const uint4* __restrict__ buf, uint64_t n_nodes, uint32_t iters,
+               unsigned long long* __restrict__ sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t quad = tid >> 2, sub = tid & 3u;
+  uint32_t acc = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+    uint4 v[kProbeInFlight];
+#pragma unroll
+    for (int k = 0; k < kProbeInFlight; ++k) {
+      const uint32_t h = mix32(quad * 0x9E3779B9u + (it * kProbeInFlight + k) * 0x632BE5ABu);
+      const uint64_t node = ((uint64_t)h * n_nodes) >> 32;  // < n_nodes
+      asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(v[k].x), "=r"(v[k].y), "=r"(v[k].z), "=r"(v[k].w)
+                   : "l"(buf + node * 4u + sub));
+    }
+#pragma unroll
+    for (int k = 0; k < kProbeInFlight; ++k) acc += v[k].x ^ v[k].w;
+  }
+  // Keeps the loads alive: the result depends on the data read, so the
+  // compiler cannot drop them (taken with probability 2^-32 per thread).
+  if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);
+}
+
+}  // namespace
+}  // namespace bits
+
+using namespace bits;
+
+extern "C" bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes,
+                                               uint64_t n_reads, double* h_nodes_per_s,
+                                               void* stream) {
+  if (!d_buf || !h_nodes_per_s) {
+    set_error("bits_probe_random_reads: NULL argument");
+    return BITS_EINVAL;
+  }
+  if (bytes < 64 || bytes % 64 || bytes >= (64ull << 32) ||
+      reinterpret_cast<uintptr_t>(d_buf) % 64) {
+    set_error("bits_probe_random_reads: the buffer must be 64-byte aligned and hold "
+              "1 .. 2^32 - 1 whole 64-byte nodes");
+    return BITS_EINVAL;
+  }
+  if (n_reads == 0 || n_reads > (1ull << 34)) {
+    set_error("bits_probe_random_reads: n_reads must be in [1, 2^34]");
+    return BITS_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t blocks = 2u * (uint32_t)sm_count();
+  const uint64_t quads = (uint64_t)blocks * kProbeBlock / 4u;
+  const uint64_t per_iter = quads * kProbeInFlight;
+  const uint32_t iters = (uint32_t)std::max<uint64_t>(1, (n_reads + per_iter - 1) / per_iter);
+  unsigned long long* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BITS_CUDA_TRY(cudaMallocAsync(&sink, sizeof(unsigned long long), st));
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) {
+    k_probe_random<<<blocks, kProbeBlock, 0, st>>>(static_cast<const uint4*>(d_buf), bytes / 64,
+                                                   iters, sink);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  cudaFreeAsync(sink, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_status(e, "bits_probe_random_reads");
+  *h_nodes_per_s = ms > 0.f ? (double)iters * (double)per_iter / (ms * 1e-3) : 0.0;
+  return BITS_OK;
+}

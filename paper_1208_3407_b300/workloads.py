@@ -9,6 +9,7 @@ Workloads (inputs from the seeded generator ``bits_synth``):
     enumerate-200k-20m  every intersecting pair of those queries and reads
     mc-100k-1m       bits_mc, 100,000 intervals vs 1,000,000, 10,000 shuffles
     allpairs-64x32   bits_count_matrix, 64 query sets x 32 databases
+    allpairs-16x8    the same on the first 16 query sets and 8 databases
     mc-screen-64x32  bits_mc_matrix over those sets, 4 shuffles, with the summary
     mc-screen-16x8   the same on the first 16 query sets and 8 databases
 
@@ -90,8 +91,10 @@ def main(argv=None):
         for _ in range(args.reps):
             ms = _timed(lambda: db.mc(a, dco, dcl, seed=7, shuffle_end=10_000, totals=totals,
                                       method=m))
-    elif args.name == "allpairs-64x32":
+    elif args.name in ("allpairs-64x32", "allpairs-16x8"):
         _, a_sets, b_sets = bits_synth.config5()
+        if args.name == "allpairs-16x8":
+            a_sets, b_sets = a_sets[:16], b_sets[:8]
         dbs = [Database(_dev(b), rmi_leaves_log2=16) for b in b_sets]
         a = [_dev(x) for x in a_sets]
         out = torch.empty((len(a), len(dbs)), dtype=torch.uint64, device="cuda")
