@@ -28,6 +28,12 @@
  *     synchronises that stream first.
  *   - Every call returns a bits_status; on failure bits_last_error() gives a
  *     message (thread-local).  No call falls back to host computation.
+ *   - A database's own storage is one cudaMalloc block, freed by bits_free.
+ *     Temporaries (sort buffers, merge-path keys, enumeration counts,
+ *     staging of pageable host buffers) come from a stream-ordered pool the
+ *     library creates per device at first use; up to 4 GiB of freed
+ *     temporaries stay reserved in it for reuse by later calls, for the
+ *     life of the process.
  */
 #ifndef BITS_H
 #define BITS_H
@@ -117,8 +123,7 @@ bits_status bits_count_method(const bits_db* db, int32_t method, const uint32_t*
  * nothing is staged.  Pageable buffers are staged through stream-ordered
  * device memory with cudaMemcpyAsync; merge path always stages.  The total
  * is added up in a stream-ordered device word of the call's own and copied
- * to h_total.  That memory comes from a pool the library creates per device
- * at the first call and keeps (up to 64 MiB reserved) for the process.  Stream-ordered like every call: with
+ * to h_total.  That memory comes from the library's temporary pool.  Stream-ordered like every call: with
  * page-locked buffers it returns at once and the results are in place when
  * `stream` has been synchronised; a pageable h_total or h_counts makes the
  * call wait for its copy, as cudaMemcpyAsync does.  Inverted queries count

@@ -64,6 +64,30 @@ int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap) {
   return b;
 }
 
+bits_status scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  int dev = 0;
+  BITS_CUDA_TRY(cudaGetDevice(&dev));
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+    if (!pools[dev]) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      BITS_CUDA_TRY(cudaMemPoolCreate(&pools[dev], &props));
+      uint64_t keep = kScratchKeepBytes;
+      BITS_CUDA_TRY(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    pool = pools[dev];
+  }
+  BITS_CUDA_TRY(cudaMallocFromPoolAsync(p, bytes, pool, st));
+  return BITS_OK;
+}
+
 bits_status cuda_status(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? BITS_ENOMEM : BITS_ECUDA;
@@ -183,8 +207,8 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
                                  align_up(sizeof(uint32_t) * kRadixHistWords, 256) +
                                  align_up(sizeof(uint32_t) * sw * 8, 256) + 256;
     void* scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, st);
-    if (e != cudaSuccess) return fail(cuda_status(e, "cudaMallocAsync(sort scratch)"));
+    const bits_status se = scratch_alloc(&scratch, scratch_bytes, st);
+    if (se != BITS_OK) return fail(se);
     char* sb = static_cast<char*>(scratch);
     ws.tmp_s = reinterpret_cast<uint32_t*>(sb);
     sb += align_up(sizeof(uint32_t) * nn, 256);
@@ -217,7 +241,7 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
       s = radix_sort_intervals(reinterpret_cast<const uint2*>(d_b), nn, db->bs, db->be, db->err,
                                ws, st);
     }
-    cudaFreeAsync(scratch, st);
+    scratch_free(scratch, st);
     if (s != BITS_OK) return fail(s);
   }
   bits_status s = build_levels(db.get(), st);

@@ -34,6 +34,16 @@ int sm_count();
 // capi.cu).
 int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap);
 bits_status cuda_status(cudaError_t e, const char* what);
+// Stream-ordered scratch for the library's own temporaries (sort buffers,
+// merge-path keys, enumeration counts, staging of host buffers), from a pool
+// the library creates per device at first use.  Freed blocks return to the
+// pool with scratch_free and up to kScratchKeepBytes stay reserved across
+// synchronisations, so repeated calls make no driver allocation.
+constexpr uint64_t kScratchKeepBytes = 4ull << 30;
+bits_status scratch_alloc(void** p, size_t bytes, cudaStream_t st);
+inline void scratch_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
 
 #define BITS_CUDA_TRY(expr)                                         \
   do {                                                              \

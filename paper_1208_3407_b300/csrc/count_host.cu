@@ -9,10 +9,7 @@
 // through a stream-ordered device buffer with cudaMemcpyAsync.  The 64-bit
 // total is added up in a stream-ordered device word of its own per call
 // (so calls on different streams do not share it) and copied back.  Both
-// come from a pool the library keeps per device.
-
-#include <mutex>
-#include <vector>
+// come from the library's scratch pool.
 
 #include "count.cuh"
 #include "db.cuh"
@@ -72,31 +69,6 @@ bits_status dispatch(const bits_db* db, int method, const uint32_t* d_a, uint32_
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Stream-ordered pool of one device for the calls' own device memory (the
-// total word, staging buffers).  Freed blocks return to it and up to 64 MiB
-// stay reserved across synchronisations, so calls in a steady state make no
-// driver allocation.  Created at the first call on a device; kept for the
-// life of the process.
-bits_status call_pool(int dev, cudaMemPool_t* out) {
-  static std::mutex mu;
-  static std::vector<cudaMemPool_t> pools;
-  std::lock_guard<std::mutex> lk(mu);
-  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
-  if (!pools[dev]) {
-    cudaMemPoolProps props{};
-    props.allocType = cudaMemAllocationTypePinned;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = dev;
-    cudaMemPool_t p = nullptr;
-    BITS_CUDA_TRY(cudaMemPoolCreate(&p, &props));
-    uint64_t keep = 64ull << 20;
-    BITS_CUDA_TRY(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
-    pools[dev] = p;
-  }
-  *out = pools[dev];
-  return BITS_OK;
-}
-
 }  // namespace
 }  // namespace bits
 
@@ -155,13 +127,11 @@ extern "C" bits_status bits_count_host(const bits_db* db, int32_t method, const 
   const size_t off_a = 256;
   const size_t off_c = off_a + (stage_a ? align256(a_bytes) : 0);
   const size_t bytes = off_c + (stage_c ? align256(c_bytes) : 0);
-  cudaMemPool_t pool = nullptr;
-  s = call_pool(cur, &pool);
-  if (s != BITS_OK) return s;
   char* buf = nullptr;
-  BITS_CUDA_TRY(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&buf), bytes, pool, st));
+  s = scratch_alloc(reinterpret_cast<void**>(&buf), bytes, st);
+  if (s != BITS_OK) return s;
   auto done = [&](bits_status r) {
-    cudaFreeAsync(buf, st);
+    scratch_free(buf, st);
     return r;
   };
   uint64_t* d_total = reinterpret_cast<uint64_t*>(buf);

@@ -205,7 +205,10 @@ bits_status run_enumerate_offsets(const bits_db* db, const uint32_t* d_a, uint32
   const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
   const size_t counts_bytes = (sizeof(uint32_t) * (size_t)n + 255) / 256 * 256;
   void* scratch = nullptr;
-  BITS_CUDA_TRY(cudaMallocAsync(&scratch, counts_bytes + sizeof(uint64_t) * (tiles + 1), st));
+  {
+    const bits_status as = scratch_alloc(&scratch, counts_bytes + sizeof(uint64_t) * (tiles + 1), st);
+    if (as != BITS_OK) return as;
+  }
   uint32_t* counts = static_cast<uint32_t*>(scratch);
   auto* part = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + counts_bytes);
   bits_status s = launch_count_search(db, d_a, n, counts, reinterpret_cast<uint64_t*>(part + tiles),
@@ -221,7 +224,7 @@ bits_status run_enumerate_offsets(const bits_db* db, const uint32_t* d_a, uint32
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) s = cuda_status(e, "enumeration offsets");
   }
-  cudaFreeAsync(scratch, st);
+  scratch_free(scratch, st);
   return s;
 }
 

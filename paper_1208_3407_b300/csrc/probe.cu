@@ -81,7 +81,10 @@ extern "C" bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes
   const uint32_t iters = (uint32_t)std::max<uint64_t>(1, (n_reads + per_iter - 1) / per_iter);
   unsigned long long* sink = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  BITS_CUDA_TRY(cudaMallocAsync(&sink, sizeof(unsigned long long), st));
+  {
+    const bits_status as = scratch_alloc(reinterpret_cast<void**>(&sink), sizeof(*sink), st);
+    if (as != BITS_OK) return as;
+  }
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -92,7 +95,7 @@ extern "C" bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-  cudaFreeAsync(sink, st);
+  scratch_free(sink, st);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   float ms = 0.f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
