@@ -1,11 +1,13 @@
 // Method choice for BITS_METHOD_AUTO.
 //
 // The first AUTO count of a size class -- (device, ceil log2 |A|, ceil log2
-// |B|, learned index built or not, per-query counts wanted or not) -- times every method the database has
-// (plain search, learned index, merge path when the query set is at least
-// 1/16 of the database) on the caller's own inputs with CUDA events,
-// three runs each after one warm-up, and keeps the fastest.  Later calls of
-// the class reuse the choice.  When BITS_AUTOTUNE_CACHE names a file, choices
+// |B|, learned index built or not, per-query counts wanted or not) -- times
+// every method the database has (plain search, learned index, merge path
+// when the query set is at least 1/16 of the database) on the caller's own
+// inputs with CUDA events: batches of back-to-back calls lasting about half
+// a millisecond, three rounds alternating the methods, fastest batch per
+// method; the fastest method wins.  Later calls of the class reuse the
+// choice.  When BITS_AUTOTUNE_CACHE names a file, choices
 // are read from it at first use and appended to it as they are made.  Under
 // stream capture no timing is possible, so the learned index (if built) or
 // the plain search is used without tuning.
@@ -115,30 +117,49 @@ bits_status autotune_count(const bits_db* db, const uint32_t* d_a, uint32_t n,
   BITS_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
   if (cs != cudaStreamCaptureStatusNone || cands.size() < 2 || n == 0) return BITS_OK;
 
-  float best = 1e30f;
-  int best_m = *method;
+  // Each candidate is timed on R back-to-back calls between one pair of
+  // events, R chosen so that a batch lasts about half a millisecond, over
+  // three rounds that alternate the candidates; its fastest batch counts.
+  // Event timestamps advance in steps of about 2 us, so single calls on a
+  // small sample are too short to tell the methods apart.
   cudaEvent_t e0, e1;
   BITS_CUDA_TRY(cudaEventCreate(&e0));
   BITS_CUDA_TRY(cudaEventCreate(&e1));
-  for (int m : cands) {
-    bits_status s = run_method(db, m, d_a, n, d_counts, d_total, st);
-    if (s != BITS_OK) return s;
-    float tot = 0.f;
-    for (int r = 0; r < 3; ++r) {
-      BITS_CUDA_TRY(cudaEventRecord(e0, st));
-      s = run_method(db, m, d_a, n, d_counts, d_total, st);
+  auto batch = [&](int m, int reps, float* ms) -> bits_status {
+    BITS_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) {
+      bits_status s = run_method(db, m, d_a, n, d_counts, d_total, st);
       if (s != BITS_OK) return s;
-      BITS_CUDA_TRY(cudaEventRecord(e1, st));
-      BITS_CUDA_TRY(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      BITS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-      tot += ms;
     }
-    if (tot < best) {
-      best = tot;
-      best_m = m;
+    BITS_CUDA_TRY(cudaEventRecord(e1, st));
+    BITS_CUDA_TRY(cudaEventSynchronize(e1));
+    BITS_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    return BITS_OK;
+  };
+  float single = 0.f;
+  for (int m : cands) {
+    float ms = 0.f;
+    bits_status s = batch(m, 2, &ms);  // warm-up, and the size of one call
+    if (s != BITS_OK) return s;
+    single = std::max(single, ms / 2.f);
+  }
+  const int reps = std::max(1, std::min(64, (int)(0.5f / std::max(single, 1e-3f)) + 1));
+  std::vector<float> best_ms(cands.size(), 1e30f);
+  for (int round = 0; round < 3; ++round) {
+    for (size_t c = 0; c < cands.size(); ++c) {
+      float ms = 0.f;
+      bits_status s = batch(cands[c], reps, &ms);
+      if (s != BITS_OK) return s;
+      best_ms[c] = std::min(best_ms[c], ms);
     }
   }
+  int best_m = cands[0];
+  float best = best_ms[0];
+  for (size_t c = 1; c < cands.size(); ++c)
+    if (best_ms[c] < best) {
+      best = best_ms[c];
+      best_m = cands[c];
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *method = best_m;
