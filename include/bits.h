@@ -328,7 +328,8 @@ bits_status bits_selftest_wait(uint32_t spin_limit, void* stream);
  * line fill, four nodes in flight per quad, timed with CUDA events.
  *   d_buf          device buffer, 64-byte aligned, `bytes` long (contents
  *                  are read, not used); much larger than L2 (e.g. 4 GiB) for
- *                  the DRAM rate.
+ *                  the DRAM rate, well inside it (e.g. 32 MiB) for the L2
+ *                  rate.
  *   bytes          a multiple of 64, at most 64 * (2^32 - 1).
  *   n_reads        node reads to issue, 1 .. 2^34 (rounded up to whole
  *                  rounds of the grid).
