@@ -28,12 +28,12 @@
  *     synchronises that stream first.
  *   - Every call returns a bits_status; on failure bits_last_error() gives a
  *     message (thread-local).  No call falls back to host computation.
- *   - A database's own storage is one cudaMalloc block, freed by bits_free.
- *     Temporaries (sort buffers, merge-path keys, enumeration counts,
- *     staging of pageable host buffers) come from a stream-ordered pool the
- *     library creates per device at first use; up to 4 GiB of freed
- *     temporaries stay reserved in it for reuse by later calls, for the
- *     life of the process.
+ *   - Device memory comes from a stream-ordered pool the library creates
+ *     per device at first use: a database's own storage (one block, freed
+ *     by bits_free) and every temporary (sort buffers, merge-path keys,
+ *     enumeration counts, staging of pageable host buffers).  Up to 4 GiB
+ *     of freed memory stays reserved in it for reuse by later calls and
+ *     databases, for the life of the process.
  */
 #ifndef BITS_H
 #define BITS_H
@@ -324,20 +324,25 @@ bits_status bits_selftest_wait(uint32_t spin_limit, void* stream);
  * which this GPU serves random 64-byte node reads, the access every search
  * kernel makes once per tree level; on a database much larger than L2 the
  * level-0 reads come from DRAM and this rate bounds the counting kernels.
- * Quads of lanes read uniformly random 64-byte nodes of d_buf with a 64-byte
- * line fill, four nodes in flight per quad, timed with CUDA events.
- *   d_buf          device buffer, 64-byte aligned, `bytes` long (contents
- *                  are read, not used); much larger than L2 (e.g. 4 GiB) for
- *                  the DRAM rate, well inside it (e.g. 32 MiB) for the L2
- *                  rate.
- *   bytes          a multiple of 64, at most 64 * (2^32 - 1).
- *   n_reads        node reads to issue, 1 .. 2^34 (rounded up to whole
- *                  rounds of the grid).
- *   h_nodes_per_s  host double receiving the node reads per second.
+ * Quads of lanes make uniformly random accesses to d_buf with a 64-byte line
+ * fill, four accesses in flight per quad, timed with CUDA events.
+ *   d_buf             device buffer, aligned to one access, `bytes` long
+ *                     (contents are read, not used); much larger than L2
+ *                     (e.g. 4 GiB) for the DRAM rate, well inside it (e.g.
+ *                     32 MiB) for the L2 rate.
+ *   bytes             a multiple of the access size, at most 2^32 - 1 accesses.
+ *   n_reads           accesses to make, 1 .. 2^34 (rounded up to whole rounds
+ *                     of the grid).
+ *   nodes_per_access  1: one 64-byte node per access; 2: both 64-byte halves
+ *                     of one random 128-byte line, read as two node loads (a
+ *                     query whose start and end searches meet in one
+ *                     interleaved node pair).
+ *   h_accesses_per_s  host double receiving the accesses per second.
  * Synchronises `stream`.
  */
 bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes, uint64_t n_reads,
-                                    double* h_nodes_per_s, void* stream);
+                                    int32_t nodes_per_access, double* h_accesses_per_s,
+                                    void* stream);
 
 /* Read-only views of the database (sorted starts, sorted ends, size). */
 bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_t** d_be,
@@ -362,7 +367,8 @@ bits_status bits_db_rmi(const bits_db* db, int32_t which, const void** d_leaves,
 /* Synchronise `stream`, then return and clear the database's device error word. */
 bits_status bits_check(const bits_db* db, void* stream);
 
-/* Release a database (NULL-safe).  Stream-ordered on the stream it was built on. */
+/* Release a database (NULL-safe): waits for all work on its device, then
+ * returns its memory to the library's pool. */
 void bits_free(bits_db* db);
 
 /* Message of the last failing call on this host thread ("" if none). */

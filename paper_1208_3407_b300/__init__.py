@@ -398,16 +398,18 @@ def mc_matrix(dbs, a_sets, contig_off: torch.Tensor, contig_len: torch.Tensor, *
     return observed, totals, (McStats(raw) if raw is not None else None)
 
 
-def probe_random_reads(nbytes: int = 4 << 30, n_reads: int = 1 << 24, *, device=None,
-                       stream=None) -> float:
+def probe_random_reads(nbytes: int = 4 << 30, n_reads: int = 1 << 24, *, pairs: bool = False,
+                       device=None, stream=None) -> float:
     """bits_probe_random_reads on a fresh ``nbytes`` device buffer: random
-    64-byte node reads per second (the bound of the search kernels on a
-    database much larger than L2)."""
+    accesses per second, each one 64-byte node (or, with ``pairs``, both
+    halves of one 128-byte line) -- the bound of the search kernels on a
+    database much larger than L2."""
     buf = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
     rate = C.c_double()
     with torch.cuda.device(buf.device):
         _lib.check(_lib.load().bits_probe_random_reads(buf.data_ptr(), nbytes, n_reads,
-                                                       C.byref(rate), _stream_ptr(stream)),
+                                                       2 if pairs else 1, C.byref(rate),
+                                                       _stream_ptr(stream)),
                    "bits_probe_random_reads")
     del buf
     return rate.value

@@ -66,7 +66,8 @@ def load():
     lib.bits_check.argtypes = [vp, vp]
     lib.bits_sort_intervals_noalloc.argtypes = [u32p, C.c_uint64, u32p, u32p, vp]
     lib.bits_selftest_wait.argtypes = [C.c_uint32, vp]
-    lib.bits_probe_random_reads.argtypes = [vp, C.c_uint64, C.c_uint64, C.POINTER(C.c_double), vp]
+    lib.bits_probe_random_reads.argtypes = [vp, C.c_uint64, C.c_uint64, C.c_int32,
+                                            C.POINTER(C.c_double), vp]
     lib.bits_enumerate_offsets.argtypes = [vp, u32p, C.c_uint64, u64p, vp]
     lib.bits_enumerate_pairs.argtypes = [vp, u32p, C.c_uint64, u64p, u32p, vp]
     lib.bits_mc_summary.argtypes = [u64p, C.c_uint32, C.c_uint32, u64p, vp, vp]

@@ -167,7 +167,7 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
     std::vector<MatDb> hd(n_db);
     uint64_t* d_tmp = nullptr;
     {
-      const bits_status as = scratch_alloc(reinterpret_cast<void**>(&d_tmp), sizeof(uint64_t), st);
+      const bits_status as = pool_alloc(reinterpret_cast<void**>(&d_tmp), sizeof(uint64_t), st);
       if (as != BITS_OK) return as;
     }
     size_t max_top = 4;
@@ -176,7 +176,7 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
       if (dbs[j]->has_rmi && n_sample) {
         bits_status s = autotune_count(dbs[j], d_as[big], n_sample, nullptr, d_tmp, st, &m);
         if (s != BITS_OK) {
-          scratch_free(d_tmp, st);
+          pool_free(d_tmp, st);
           return s;
         }
       }
@@ -187,7 +187,7 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
       hd[j].err = dbs[j]->err;
       if (m != BITS_METHOD_RMI) max_top = std::max<size_t>(max_top, top_words(dbs[j]->lvl.top_size));
     }
-    scratch_free(d_tmp, st);
+    pool_free(d_tmp, st);
     // Units: largest database first, then set by set, kChunk queries each.
     std::vector<uint32_t> order(n_db);
     for (uint32_t j = 0; j < n_db; ++j) order[j] = j;

@@ -64,7 +64,7 @@ int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap) {
   return b;
 }
 
-bits_status scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+bits_status pool_alloc(void** p, size_t bytes, cudaStream_t st) {
   static std::mutex mu;
   static std::vector<cudaMemPool_t> pools;
   int dev = 0;
@@ -79,7 +79,7 @@ bits_status scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
       props.location.type = cudaMemLocationTypeDevice;
       props.location.id = dev;
       BITS_CUDA_TRY(cudaMemPoolCreate(&pools[dev], &props));
-      uint64_t keep = kScratchKeepBytes;
+      uint64_t keep = kPoolKeepBytes;
       BITS_CUDA_TRY(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
     }
     pool = pools[dev];
@@ -168,14 +168,17 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   const size_t off_bs = 0;
   const size_t off_be = align_up(off_bs + sizeof(uint32_t) * n16, 256);
   const size_t off_lv = align_up(off_be + sizeof(uint32_t) * n16, 256);
-  const size_t off_top = align_up(off_lv + sizeof(uint32_t) * 2 * db->plan.level_words, 256);
+  const size_t off_top = align_up(off_lv + sizeof(uint32_t) * db->plan.level_words, 256);
   const size_t off_err = align_up(off_top + sizeof(uint32_t) * 2 * db->plan.top_size, 256);
   const size_t off_rmi = align_up(off_err + 256, 256);
   const size_t leaves = db->has_rmi ? (1ull << o.rmi_leaves_log2) : 0;
   const size_t off_enum = align_up(off_rmi + 2 * leaves * sizeof(bits_rmi_leaf), 256);
   const size_t total = off_enum + (want_enum ? sizeof(uint2) * std::max<uint32_t>(nn, 1) : 0);
   void* block = nullptr;
-  BITS_CUDA_TRY(cudaMalloc(&block, total));
+  {
+    const bits_status as = pool_alloc(&block, total, st);
+    if (as != BITS_OK) return as;
+  }
   db->block = block;
   db->block_bytes = total;
   char* base = static_cast<char*>(block);
@@ -207,7 +210,7 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
                                  align_up(sizeof(uint32_t) * kRadixHistWords, 256) +
                                  align_up(sizeof(uint32_t) * sw * 8, 256) + 256;
     void* scratch = nullptr;
-    const bits_status se = scratch_alloc(&scratch, scratch_bytes, st);
+    const bits_status se = pool_alloc(&scratch, scratch_bytes, st);
     if (se != BITS_OK) return fail(se);
     char* sb = static_cast<char*>(scratch);
     ws.tmp_s = reinterpret_cast<uint32_t*>(sb);
@@ -241,7 +244,7 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
       s = radix_sort_intervals(reinterpret_cast<const uint2*>(d_b), nn, db->bs, db->be, db->err,
                                ws, st);
     }
-    scratch_free(scratch, st);
+    pool_free(scratch, st);
     if (s != BITS_OK) return fail(s);
   }
   bits_status s = build_levels(db.get(), st);
@@ -534,6 +537,9 @@ void bits_free(bits_db* db) {
   release_mc_graphs(db);
   release_matrix_graphs(db);
   release_mc_matrix_graphs(db);
+  // The block comes from the stream-ordered pool, and cudaFree does not wait
+  // for such memory: finish every stream's work on the device first.
+  cudaDeviceSynchronize();
   cudaFree(db->block);
   if (prev != db->device) cudaSetDevice(prev);
   delete db;

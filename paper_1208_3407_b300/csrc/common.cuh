@@ -34,14 +34,15 @@ int sm_count();
 // capi.cu).
 int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap);
 bits_status cuda_status(cudaError_t e, const char* what);
-// Stream-ordered scratch for the library's own temporaries (sort buffers,
-// merge-path keys, enumeration counts, staging of host buffers), from a pool
-// the library creates per device at first use.  Freed blocks return to the
-// pool with scratch_free and up to kScratchKeepBytes stay reserved across
-// synchronisations, so repeated calls make no driver allocation.
-constexpr uint64_t kScratchKeepBytes = 4ull << 30;
-bits_status scratch_alloc(void** p, size_t bytes, cudaStream_t st);
-inline void scratch_free(void* p, cudaStream_t st) {
+// Device memory from the library's stream-ordered pool, one per device,
+// created at first use: database blocks and every temporary (sort buffers,
+// merge-path keys, enumeration counts, staging of host buffers).  Freed
+// blocks return to the pool (pool_free, or cudaFree for a database) and up
+// to kPoolKeepBytes stay reserved across synchronisations, so repeated
+// calls and rebuilt databases make no driver allocation.
+constexpr uint64_t kPoolKeepBytes = 4ull << 30;
+bits_status pool_alloc(void** p, size_t bytes, cudaStream_t st);
+inline void pool_free(void* p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
 }
 

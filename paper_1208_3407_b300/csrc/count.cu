@@ -69,6 +69,7 @@ struct LevelJob {
   uint32_t count;       // entries to write (real + padding)
   uint32_t real;        // real entries; the rest are 0xFFFFFFFF
   int shift;            // 4 * level
+  int half;             // 0: plain; 1 / 2: the starts' / ends' half of interleaved node pairs
 };
 struct LevelJobs {
   LevelJob j[2 * (kMaxLevels + 2)];
@@ -79,14 +80,26 @@ __global__ void k_build_levels(LevelJobs jobs, uint32_t n) {
   uint32_t* out = J->out;
   const uint32_t* src = J->src;
   const uint32_t count = J->count, real = J->real;
-  const int shift = J->shift;
+  const int shift = J->shift, half = J->half;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     uint32_t v = kU32Max;
     if (i < real) {
       const uint64_t end = min(((uint64_t)i + 1u) << shift, (uint64_t)n);
       v = src[end - 1];
     }
-    out[i] = v;
+    const uint32_t at = half ? 32u * (i >> 4) + 16u * (uint32_t)(half - 1) + (i & 15u) : i;
+    out[at] = v;
+  }
+}
+
+// Level 0 of both sorted arrays (already padded to 16) into node pairs:
+// eight lanes move one 128-byte pair with 16-byte loads and stores.
+__global__ void k_interleave_level0(const uint4* __restrict__ bs, const uint4* __restrict__ be,
+                                    uint32_t pairs, uint4* __restrict__ out) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < 8u * pairs; t += stride) {
+    const uint32_t p = t >> 3, q = t & 7u;
+    out[t] = q < 4u ? bs[4u * p + q] : be[4u * p + (q - 4u)];
   }
 }
 
@@ -120,11 +133,12 @@ void plan_levels(uint32_t n, int top_log2, LevelPlan& p) {
   uint32_t ts = 4;
   while (ts < p.len[J] + 1u) ts <<= 1;
   p.top_size = ts;
-  // words of the stored levels 1 .. J-1 (per array), each padded to 16
+  // words of the stored levels 0 .. J-1, both arrays interleaved by node,
+  // each level padded to 16 entries per array
   size_t words = 0;
-  for (int j = 1; j < J; ++j) {
+  for (int j = 0; j < J; ++j) {
     p.off[j] = words;
-    words += round16(p.len[j]);
+    words += 2 * (size_t)round16(p.len[j]);
   }
   p.level_words = words;
 }
@@ -136,27 +150,34 @@ bits_status build_levels(bits_db* db, cudaStream_t st) {
   L.top_size = p.top_size;
   L.top = db->top;
   for (int j = 0; j <= p.J; ++j) L.len[j] = p.len[j];
-  for (int a = 0; a < 2; ++a) {
-    uint32_t* X = a ? db->be : db->bs;
-    L.lv[a][0] = X;
-    for (int j = 1; j < p.J; ++j) L.lv[a][j] = db->levels + a * p.level_words + p.off[j];
-  }
+  L.x[0] = db->bs;
+  L.x[1] = db->be;
+  for (int j = 0; j < p.J; ++j) L.il[j] = db->levels + p.off[j];
   LevelJobs jobs{};
   int nj = 0;
   for (int a = 0; a < 2; ++a) {
     uint32_t* X = a ? db->be : db->bs;
-    // level 0 padding
-    jobs.j[nj++] = LevelJob{X + db->n, X, round16(db->n) - db->n, 0u, 0};
+    // padding of the plain sorted array
+    jobs.j[nj++] = LevelJob{X + db->n, X, round16(db->n) - db->n, 0u, 0, 0};
     for (int j = 1; j < p.J; ++j)
-      jobs.j[nj++] = LevelJob{db->levels + a * p.level_words + p.off[j], X, round16(p.len[j]),
-                              p.len[j], 4 * j};
-    jobs.j[nj++] = LevelJob{db->top + a * p.top_size, X, p.top_size, p.len[p.J], 4 * p.J};
+      jobs.j[nj++] = LevelJob{db->levels + p.off[j], X, round16(p.len[j]), p.len[j], 4 * j, a + 1};
+    jobs.j[nj++] = LevelJob{db->top + a * p.top_size, X, p.top_size, p.len[p.J], 4 * p.J, 0};
   }
   uint32_t biggest = 1;
   for (int k = 0; k < nj; ++k) biggest = std::max(biggest, jobs.j[k].count);
   const dim3 grid(std::min<uint32_t>((biggest + 255) / 256, 4096), nj);
   k_build_levels<<<grid, 256, 0, st>>>(jobs, db->n);
   BITS_LAUNCH_CHECK("k_build_levels");
+  if (p.J > 0) {
+    // Runs after the padding of the plain arrays above (stream order).
+    const uint32_t pairs = round16(db->n) / 16u;
+    const uint32_t blocks =
+        std::min<uint32_t>((8u * pairs + 255u) / 256u, (uint32_t)(sm_count() * 8));
+    k_interleave_level0<<<blocks, 256, 0, st>>>(reinterpret_cast<const uint4*>(db->bs),
+                                                reinterpret_cast<const uint4*>(db->be), pairs,
+                                                reinterpret_cast<uint4*>(db->levels + p.off[0]));
+    BITS_LAUNCH_CHECK("k_interleave_level0");
+  }
   return BITS_OK;
 }
 

@@ -128,10 +128,10 @@ extern "C" bits_status bits_count_host(const bits_db* db, int32_t method, const 
   const size_t off_c = off_a + (stage_a ? align256(a_bytes) : 0);
   const size_t bytes = off_c + (stage_c ? align256(c_bytes) : 0);
   char* buf = nullptr;
-  s = scratch_alloc(reinterpret_cast<void**>(&buf), bytes, st);
+  s = pool_alloc(reinterpret_cast<void**>(&buf), bytes, st);
   if (s != BITS_OK) return s;
   auto done = [&](bits_status r) {
-    scratch_free(buf, st);
+    pool_free(buf, st);
     return r;
   };
   uint64_t* d_total = reinterpret_cast<uint64_t*>(buf);

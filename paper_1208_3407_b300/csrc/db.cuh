@@ -38,8 +38,8 @@ struct bits_mc_graph;  // cached CUDA graph of one bits_mc argument set (mc.cu)
 struct LevelPlan {
   int J = 0;                           // top level, kept in shared memory
   uint32_t len[bits::kMaxLevels + 1] = {};
-  size_t off[bits::kMaxLevels] = {};   // word offset of level j (1 <= j < J) in one array's storage
-  size_t level_words = 0;              // words of levels 1 .. J-1 per array
+  size_t off[bits::kMaxLevels] = {};   // word offset of level j (0 <= j < J) in the level storage
+  size_t level_words = 0;              // words of levels 0 .. J-1, both arrays interleaved
   uint32_t top_size = 4;               // shared-memory entries per array (power of two)
 };
 
@@ -48,7 +48,7 @@ struct bits_db {
   uint32_t n = 0;
   uint32_t* bs = nullptr;      // sorted starts, padded with 0xFFFFFFFF to 16 (device)
   uint32_t* be = nullptr;      // sorted ends, padded the same way (device)
-  uint32_t* levels = nullptr;  // levels 1 .. J-1 of both arrays (device)
+  uint32_t* levels = nullptr;  // levels 0 .. J-1 of both arrays, interleaved by node (device)
   uint32_t* top = nullptr;     // top-level images [2][top_size] (device)
   LevelPlan plan;
   bits::LevelIndex lvl{};      // kernel-side view of the levels

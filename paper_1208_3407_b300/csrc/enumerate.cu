@@ -206,7 +206,7 @@ bits_status run_enumerate_offsets(const bits_db* db, const uint32_t* d_a, uint32
   const size_t counts_bytes = (sizeof(uint32_t) * (size_t)n + 255) / 256 * 256;
   void* scratch = nullptr;
   {
-    const bits_status as = scratch_alloc(&scratch, counts_bytes + sizeof(uint64_t) * (tiles + 1), st);
+    const bits_status as = pool_alloc(&scratch, counts_bytes + sizeof(uint64_t) * (tiles + 1), st);
     if (as != BITS_OK) return as;
   }
   uint32_t* counts = static_cast<uint32_t*>(scratch);
@@ -224,7 +224,7 @@ bits_status run_enumerate_offsets(const bits_db* db, const uint32_t* d_a, uint32
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) s = cuda_status(e, "enumeration offsets");
   }
-  scratch_free(scratch, st);
+  pool_free(scratch, st);
   return s;
 }
 

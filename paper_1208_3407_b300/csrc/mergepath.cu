@@ -141,7 +141,7 @@ bits_status launch_count_mergepath(const bits_db* db, const uint32_t* d_a, uint3
                        2 * align256(sizeof(uint32_t) * (tiles + 1));
   void* scratch = nullptr;
   {
-    const bits_status as = scratch_alloc(&scratch, bytes, st);
+    const bits_status as = pool_alloc(&scratch, bytes, st);
     if (as != BITS_OK) return as;
   }
   char* p = static_cast<char*>(scratch);
@@ -173,7 +173,7 @@ bits_status launch_count_mergepath(const bits_db* db, const uint32_t* d_a, uint3
   ws.tmp_s = spec[0].tmp_keys;
   ws.tmp_e = spec[1].tmp_keys;
   auto done = [&](bits_status s) {
-    scratch_free(scratch, st);
+    pool_free(scratch, st);
     return s;
   };
 

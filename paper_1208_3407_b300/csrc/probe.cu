@@ -7,9 +7,11 @@
 // random, and the rate of such reads, not the byte bandwidth, bounds the
 // kernels: random 64-byte reads reach about a third of the copy bandwidth.
 // This probe issues exactly that access -- quads reading uniformly random
-// nodes of a buffer, four independent nodes in flight per quad -- and times
-// it with CUDA events, so the search kernels can be set against the same
-// hardware limit.
+// nodes of a buffer, four independent accesses in flight per quad -- and
+// times it with CUDA events, so the search kernels can be set against the
+// same hardware limit.  In pair mode every access reads both 64-byte halves
+// of one random 128-byte line, as a query does whose two searches (starts
+// and ends) meet in one interleaved node pair.
 #include "common.cuh"
 
 namespace bits {
@@ -28,24 +30,36 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   return x;
 }
 
+// kPair = false: one 64-byte node per random access.  kPair = true: both
+// 64-byte halves of one random 128-byte line, read as two node loads -- the
+// access of a query whose two searches meet in one interleaved node pair.
+template <bool kPair>
 __global__ void __launch_bounds__(kProbeBlock)
-k_probe_random(const uint4* __restrict__ buf, uint64_t n_nodes, uint32_t iters,
+k_probe_random(const uint4* __restrict__ buf, uint64_t n_units, uint32_t iters,
                unsigned long long* __restrict__ sink) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t quad = tid >> 2, sub = tid & 3u;
   uint32_t acc = 0;
   for (uint32_t it = 0; it < iters; ++it) {
-    uint4 v[kProbeInFlight];
+    uint4 v[kProbeInFlight], w[kProbeInFlight];
 #pragma unroll
     for (int k = 0; k < kProbeInFlight; ++k) {
       const uint32_t h = mix32(quad * 0x9E3779B9u + (it * kProbeInFlight + k) * 0x632BE5ABu);
-      const uint64_t node = ((uint64_t)h * n_nodes) >> 32;  // < n_nodes
+      const uint64_t unit = ((uint64_t)h * n_units) >> 32;  // < n_units
+      const uint4* p = buf + unit * (kPair ? 8u : 4u) + sub;
       asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
                    : "=r"(v[k].x), "=r"(v[k].y), "=r"(v[k].z), "=r"(v[k].w)
-                   : "l"(buf + node * 4u + sub));
+                   : "l"(p));
+      if (kPair) {
+        asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(w[k].x), "=r"(w[k].y), "=r"(w[k].z), "=r"(w[k].w)
+                     : "l"(p + 4));
+      } else {
+        w[k] = make_uint4(0u, 0u, 0u, 0u);
+      }
     }
 #pragma unroll
-    for (int k = 0; k < kProbeInFlight; ++k) acc += v[k].x ^ v[k].w;
+    for (int k = 0; k < kProbeInFlight; ++k) acc += v[k].x ^ v[k].w ^ w[k].y;
   }
   // Keeps the loads alive: the result depends on the data read, so the
   // compiler cannot drop them (taken with probability 2^-32 per thread).
@@ -58,16 +72,21 @@ k_probe_random(const uint4* __restrict__ buf, uint64_t n_nodes, uint32_t iters,
 using namespace bits;
 
 extern "C" bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes,
-                                               uint64_t n_reads, double* h_nodes_per_s,
-                                               void* stream) {
-  if (!d_buf || !h_nodes_per_s) {
+                                               uint64_t n_reads, int32_t nodes_per_access,
+                                               double* h_accesses_per_s, void* stream) {
+  if (!d_buf || !h_accesses_per_s) {
     set_error("bits_probe_random_reads: NULL argument");
     return BITS_EINVAL;
   }
-  if (bytes < 64 || bytes % 64 || bytes >= (64ull << 32) ||
-      reinterpret_cast<uintptr_t>(d_buf) % 64) {
-    set_error("bits_probe_random_reads: the buffer must be 64-byte aligned and hold "
-              "1 .. 2^32 - 1 whole 64-byte nodes");
+  if (nodes_per_access != 1 && nodes_per_access != 2) {
+    set_error("bits_probe_random_reads: nodes_per_access must be 1 or 2");
+    return BITS_EINVAL;
+  }
+  const uint64_t unit = 64ull * (uint64_t)nodes_per_access;
+  if (bytes < unit || bytes % unit || bytes / unit >= (1ull << 32) ||
+      reinterpret_cast<uintptr_t>(d_buf) % unit) {
+    set_error("bits_probe_random_reads: the buffer must be aligned to and hold 1 .. 2^32 - 1 "
+              "whole accesses (64 bytes, or 128 with two nodes per access)");
     return BITS_EINVAL;
   }
   if (n_reads == 0 || n_reads > (1ull << 34)) {
@@ -82,26 +101,29 @@ extern "C" bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes
   unsigned long long* sink = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   {
-    const bits_status as = scratch_alloc(reinterpret_cast<void**>(&sink), sizeof(*sink), st);
+    const bits_status as = pool_alloc(reinterpret_cast<void**>(&sink), sizeof(*sink), st);
     if (as != BITS_OK) return as;
   }
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
   if (e == cudaSuccess) {
-    k_probe_random<<<blocks, kProbeBlock, 0, st>>>(static_cast<const uint4*>(d_buf), bytes / 64,
-                                                   iters, sink);
+    const uint4* b = static_cast<const uint4*>(d_buf);
+    if (nodes_per_access == 2)
+      k_probe_random<true><<<blocks, kProbeBlock, 0, st>>>(b, bytes / unit, iters, sink);
+    else
+      k_probe_random<false><<<blocks, kProbeBlock, 0, st>>>(b, bytes / unit, iters, sink);
     count_launch();
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-  scratch_free(sink, st);
+  pool_free(sink, st);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   float ms = 0.f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_status(e, "bits_probe_random_reads");
-  *h_nodes_per_s = ms > 0.f ? (double)iters * (double)per_iter / (ms * 1e-3) : 0.0;
+  *h_accesses_per_s = ms > 0.f ? (double)iters * (double)per_iter / (ms * 1e-3) : 0.0;
   return BITS_OK;
 }

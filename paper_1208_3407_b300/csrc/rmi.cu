@@ -229,14 +229,14 @@ bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t
   const size_t bytes = off_sums + sizeof(double) * 4 * (size_t)L;
   void* scratch = nullptr;
   {
-    const bits_status as = scratch_alloc(&scratch, bytes, st);
+    const bits_status as = pool_alloc(&scratch, bytes, st);
     if (as != BITS_OK) return as;
   }
   double* root_sums = static_cast<double*>(scratch);
   uint32_t* lo = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) + off_lo);
   double* leaf_sums = reinterpret_cast<double*>(static_cast<char*>(scratch) + off_sums);
   auto done = [&](bits_status s) {
-    scratch_free(scratch, st);
+    pool_free(scratch, st);
     return s;
   };
   if (cudaMemsetAsync(scratch, 0, bytes, st) != cudaSuccess)

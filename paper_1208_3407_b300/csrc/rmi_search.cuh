@@ -78,25 +78,38 @@ __device__ __forceinline__ int rmi_entry_level(int J, uint32_t wl, uint32_t wh, 
   return J + 1;
 }
 
-// Finish one search: r is the descent's result for entry level j (<= J), or
-// unused when j > J (then the window is searched here).  Checks the block
-// edges and falls back to a full binary search when a check fails.
-__device__ __forceinline__ uint32_t rmi_finish(const uint32_t* __restrict__ X, uint32_t n,
+// Key k of sorted array a (0: starts, 1: ends), read from the interleaved
+// level 0 the descents use (so the check below touches the same lines), or
+// from the plain array when no level is stored (J = 0).
+__device__ __forceinline__ uint32_t level0_key(const LevelIndex& L, int a, uint32_t k) {
+  return L.J > 0 ? __ldg(L.il[0] + 32u * (k >> 4) + 16u * (uint32_t)a + (k & 15u))
+                 : __ldg(L.x[a] + k);
+}
+
+// #(X_a < key) by a binary search over ranks [lo, lo + len).
+__device__ __forceinline__ uint32_t level0_lower_bound(const LevelIndex& L, int a, uint32_t lo,
+                                                       uint32_t len, uint32_t key) {
+  while (len > 0) {
+    const uint32_t half = len >> 1;
+    if (level0_key(L, a, lo + half) < key) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  return lo;
+}
+
+// Finish one search of array a: r is the descent's result for entry level
+// j (<= J), or unused when j > J (then the window is searched here).  Checks
+// the block edges and falls back to a full binary search when a check fails.
+__device__ __forceinline__ uint32_t rmi_finish(const LevelIndex& L, int a, uint32_t n,
                                                uint32_t key, int j, int J, uint32_t r,
                                                uint32_t wl, uint32_t wh) {
   uint32_t edge_lo, edge_hi;
   if (j > J) {
-    uint32_t lo = wl, len = wh - wl;
-    while (len > 0) {
-      const uint32_t half = len >> 1;
-      if (__ldg(X + lo + half) < key) {
-        lo += half + 1;
-        len -= half + 1;
-      } else {
-        len = half;
-      }
-    }
-    r = lo;
+    r = level0_lower_bound(L, a, wl, wh - wl, key);
     edge_lo = wl;
     edge_hi = wh;
   } else {
@@ -105,9 +118,9 @@ __device__ __forceinline__ uint32_t rmi_finish(const uint32_t* __restrict__ X, u
     edge_hi = (uint32_t)min((unsigned long long)edge_lo + (1ull << sh), (unsigned long long)n);
   }
   bool ok = true;
-  if (r == edge_lo && r > 0u) ok = __ldg(X + r - 1u) < key;
-  if (ok && r == edge_hi && r < n) ok = __ldg(X + r) >= key;
-  return ok ? r : rank_lt_global(X, n, key);
+  if (r == edge_lo && r > 0u) ok = level0_key(L, a, r - 1u) < key;
+  if (ok && r == edge_hi && r < n) ok = level0_key(L, a, r) >= key;
+  return ok ? r : level0_lower_bound(L, a, 0u, n, key);
 }
 
 // Both ranks of one thread's query through the learned index (all 32 lanes
@@ -124,8 +137,8 @@ __device__ __forceinline__ void rmi_rank2(const RmiView& R, const LevelIndex& L,
   uint32_t is = ds ? wls >> (4 * ds) : 0u, ie = de ? wle >> (4 * de) : 0u;
   const int jmax = __reduce_max_sync(0xFFFFFFFFu, max(ds, de));
   if (jmax > 0) quad_descend_from(L, jmax, ds, is, key_s, de, ie, key_e, stream_level0);
-  rs = rmi_finish(L.lv[0][0], nb, key_s, js, L.J, is, wls, whs);
-  re = rmi_finish(L.lv[1][0], nb, key_e, je, L.J, ie, wle, whe);
+  rs = rmi_finish(L, 0, nb, key_s, js, L.J, is, wls, whs);
+  re = rmi_finish(L, 1, nb, key_e, je, L.J, ie, wle, whe);
 }
 
 }  // namespace bits

@@ -11,13 +11,18 @@
 //     level 0      = X itself, padded with 0xFFFFFFFF to a multiple of 16
 //     level j >= 1 : L_j[i] = X[min((i+1) * 16^j, n) - 1], the last key of
 //                    the i-th block of 16^j keys; also padded to 16 entries.
-// L_j[i] is the last real entry of the 64-byte chunk L_{j-1}[16i, 16i+16),
-// so if i = #(L_j < key) then #(L_{j-1} < key) = 16 i + #(chunk < key).
-// The top level J (at most 8191 entries) lives in shared memory and is
-// searched per thread; every lower level costs one 64-byte chunk, loaded by
-// the four lanes of a quad (16 bytes each, fully coalesced) and counted with
-// two shuffles.  Only the level-0 chunk normally comes from DRAM; the
-// levels above it are 1/16, 1/256, ... of the array and stay in L2.
+// L_j[i] is the last real entry of the 64-byte node L_{j-1}[16i, 16i+16),
+// so if i = #(L_j < key) then #(L_{j-1} < key) = 16 i + #(node < key).
+// The top level J (at most 16383 entries) lives in shared memory and is
+// searched per thread; every lower level costs one 64-byte node per search,
+// loaded by the four lanes of a quad (16 bytes each, fully coalesced) and
+// counted with two shuffles.  Levels 0 .. J-1 are stored interleaved: node
+// i of the starts' level j and node i of the ends' level j share one
+// 128-byte line.  The two ranks of a query differ by its count, so for
+// queries that meet few database intervals both searches read the same
+// node index, and the pair costs one random DRAM line instead of two.
+// Only the level-0 nodes normally come from DRAM; the levels above them
+// are 1/16, 1/256, ... of the array and stay in L2.
 #pragma once
 
 #include "common.cuh"
@@ -27,7 +32,10 @@ namespace bits {
 constexpr int kMaxLevels = 6;  // J <= 5 for n < 2^30 with a 8191-entry top
 
 struct LevelIndex {
-  const uint32_t* lv[2][kMaxLevels];  // [array][j]: storage of level j (j < J); [a][0] = X
+  const uint32_t* x[2];               // the sorted arrays B_S, B_E (padded to 16)
+  const uint32_t* il[kMaxLevels];     // level j < J of both arrays, interleaved by node:
+                                      // node i of the starts at il[j] + 32 i, of the ends
+                                      // at il[j] + 32 i + 16
   uint32_t len[kMaxLevels + 1];       // real entries of level j, j <= J
   const uint32_t* top;                // top level image: [2][top_size], padded with 0xFFFFFFFF
   uint32_t top_size;                  // power of two >= len[J] + 1, >= 4
@@ -147,15 +155,15 @@ __device__ __forceinline__ void quad_descend_from(const LevelIndex& L, int jmax,
   for (int j = kMaxLevels - 1; j >= 1; --j) {
     if (j > jmax) continue;
     const uint32_t lenj = L.len[j], lenm = L.len[j - 1];
-    const uint32_t* LS = L.lv[0][j - 1];
-    const uint32_t* LE = L.lv[1][j - 1];
+    const uint32_t* LS = L.il[j - 1];
+    const uint32_t* LE = LS + 16;
     const uint64_t pol = j == 1 ? pol_first : pol_last;
     uint4 vs[4], ve[4];
     #pragma unroll
     for (int o = 0; o < 4; ++o) {
-      vs[o] = (j <= jss[o] && is[o] < lenj) ? ldg4_hint(LS + 16u * is[o] + 4u * sub, pol)
+      vs[o] = (j <= jss[o] && is[o] < lenj) ? ldg4_hint(LS + 32u * is[o] + 4u * sub, pol)
                                             : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
-      ve[o] = (j <= jes[o] && ie[o] < lenj) ? ldg4_hint(LE + 16u * ie[o] + 4u * sub, pol)
+      ve[o] = (j <= jes[o] && ie[o] < lenj) ? ldg4_hint(LE + 32u * ie[o] + 4u * sub, pol)
                                             : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
     }
     #pragma unroll
@@ -194,15 +202,15 @@ __device__ __forceinline__ void quad_descend(const LevelIndex& L, uint32_t& is_o
   for (int j = kMaxLevels - 1; j >= 1; --j) {
     if (j > L.J) continue;
     const uint32_t lenj = L.len[j], lenm = L.len[j - 1];
-    const uint32_t* LS = L.lv[0][j - 1];
-    const uint32_t* LE = L.lv[1][j - 1];
+    const uint32_t* LS = L.il[j - 1];
+    const uint32_t* LE = LS + 16;
     const uint64_t pol = j == 1 ? pol_first : pol_last;
     uint4 vs[4], ve[4];
     #pragma unroll
     for (int o = 0; o < 4; ++o) {
-      vs[o] = is[o] < lenj ? ldg4_hint(LS + 16u * is[o] + 4u * sub, pol)
+      vs[o] = is[o] < lenj ? ldg4_hint(LS + 32u * is[o] + 4u * sub, pol)
                            : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
-      ve[o] = ie[o] < lenj ? ldg4_hint(LE + 16u * ie[o] + 4u * sub, pol)
+      ve[o] = ie[o] < lenj ? ldg4_hint(LE + 32u * ie[o] + 4u * sub, pol)
                            : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
     }
     #pragma unroll
@@ -218,23 +226,6 @@ __device__ __forceinline__ void quad_descend(const LevelIndex& L, uint32_t& is_o
   }
   is_out = sub == 0 ? is[0] : sub == 1 ? is[1] : sub == 2 ? is[2] : is[3];
   ie_out = sub == 0 ? ie[0] : sub == 1 ? ie[1] : sub == 2 ? ie[2] : ie[3];
-}
-
-// #(X[0 .. n) < key) by a per-thread binary search straight in global
-// memory: the slow exact path the learned index falls back to.
-__device__ __forceinline__ uint32_t rank_lt_global(const uint32_t* __restrict__ X, uint32_t n,
-                                                   uint32_t key) {
-  uint32_t lo = 0, len = n;
-  while (len > 0) {
-    const uint32_t half = len >> 1;
-    if (__ldg(X + lo + half) < key) {
-      lo += half + 1;
-      len -= half + 1;
-    } else {
-      len = half;
-    }
-  }
-  return lo;
 }
 
 // ICount of query [s, e) from its two ranks.

@@ -36,7 +36,7 @@ extern "C" bits_status bits_selftest_wait(uint32_t spin_limit, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t* d = nullptr;
   {
-    const bits_status as = scratch_alloc(reinterpret_cast<void**>(&d), 2 * sizeof(uint32_t), st);
+    const bits_status as = pool_alloc(reinterpret_cast<void**>(&d), 2 * sizeof(uint32_t), st);
     if (as != BITS_OK) return as;
   }
   BITS_CUDA_TRY(cudaMemsetAsync(d, 0, 2 * sizeof(uint32_t), st));
@@ -45,7 +45,7 @@ extern "C" bits_status bits_selftest_wait(uint32_t spin_limit, void* stream) {
   uint32_t h = 0;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-  scratch_free(d, st);
+  pool_free(d, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "bits_selftest_wait");
   if (h & DEV_ERR_TIMEOUT) {

@@ -55,10 +55,15 @@ def test_host_side_argument_checks(lib):
     assert lib.bits_count(None, None, 0, None, None, None) == _lib.BITS_EINVAL
     assert lib.bits_count_host(None, 1, None, 0, None, None, None) == _lib.BITS_EINVAL
     rate = C.c_double()
-    assert lib.bits_probe_random_reads(None, 1 << 20, 1, C.byref(rate), None) == _lib.BITS_EINVAL
-    assert lib.bits_probe_random_reads(C.c_void_p(256), 100, 1, C.byref(rate),
+    assert lib.bits_probe_random_reads(None, 1 << 20, 1, 1, C.byref(rate),
                                        None) == _lib.BITS_EINVAL
-    assert lib.bits_probe_random_reads(C.c_void_p(256), 1 << 20, 0, C.byref(rate),
+    assert lib.bits_probe_random_reads(C.c_void_p(256), 100, 1, 1, C.byref(rate),
+                                       None) == _lib.BITS_EINVAL
+    assert lib.bits_probe_random_reads(C.c_void_p(256), 1 << 20, 0, 1, C.byref(rate),
+                                       None) == _lib.BITS_EINVAL
+    assert lib.bits_probe_random_reads(C.c_void_p(256), 1 << 20, 1, 3, C.byref(rate),
+                                       None) == _lib.BITS_EINVAL
+    assert lib.bits_probe_random_reads(C.c_void_p(64), 1 << 20, 1, 2, C.byref(rate),
                                        None) == _lib.BITS_EINVAL
     assert lib.bits_check(None, None) == _lib.BITS_EINVAL
     assert lib.bits_db_info(None, None, None, None, None) == _lib.BITS_EINVAL

@@ -23,6 +23,11 @@ def test_dram_rate_is_plausible_and_below_l2_rate(bits):
     assert 1e9 < dram < 6.4e12 / 64
     # A buffer inside the 126 MB L2 is served faster than one 30x larger.
     assert l2 > 1.5 * dram
+    # Both halves of a random 128-byte line: at most the byte rate allows,
+    # and no more accesses per second than single nodes.
+    pairs = max(bits.probe_random_reads(4 << 30, 1 << 24, pairs=True) for _ in range(2))
+    assert 1e9 < pairs < 6.4e12 / 128
+    assert pairs < 1.1 * dram
 
 
 def test_argument_errors(bits):
@@ -31,9 +36,13 @@ def test_argument_errors(bits):
     lib = _lib.load()
     buf = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     rate = C.c_double()
-    assert lib.bits_probe_random_reads(buf.data_ptr(), 1000, 16, C.byref(rate), None) == 1
-    assert lib.bits_probe_random_reads(buf.data_ptr() + 16, 1 << 16, 16, C.byref(rate),
+    assert lib.bits_probe_random_reads(buf.data_ptr(), 1000, 16, 1, C.byref(rate), None) == 1
+    assert lib.bits_probe_random_reads(buf.data_ptr() + 16, 1 << 16, 16, 1, C.byref(rate),
                                        None) == 1
-    assert lib.bits_probe_random_reads(buf.data_ptr(), 1 << 20, 1 << 16, C.byref(rate),
+    assert lib.bits_probe_random_reads(buf.data_ptr() + 64, 1 << 16, 16, 2, C.byref(rate),
+                                       None) == 1
+    assert lib.bits_probe_random_reads(buf.data_ptr(), 1 << 20, 1 << 16, 1, C.byref(rate),
+                                       None) == 0
+    assert lib.bits_probe_random_reads(buf.data_ptr(), 1 << 20, 1 << 16, 2, C.byref(rate),
                                        None) == 0
     assert rate.value > 0
