@@ -6,8 +6,10 @@
 // coalesced 4-byte store of the count, and a block reduction of the 64-bit
 // total with one atomic per CTA.
 //
-// Also here: k_build_levels, which writes the implicit 16-ary tree of both
-// sorted arrays after the sort.
+// Also here: k_build_levels and k_interleave_level0, which write the
+// implicit 16-ary tree of both sorted arrays after the sort, its levels
+// stored with node i of the starts and node i of the ends in one 128-byte
+// line (search.cuh).
 #include "count.cuh"
 #include "search.cuh"
 
