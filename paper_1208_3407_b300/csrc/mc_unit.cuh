@@ -20,6 +20,7 @@ namespace bits {
 constexpr int kMcBlock = 256;    // shuffles per work unit (one per thread)
 constexpr int kMcChunk = 1024;   // intervals per work unit
 constexpr int kMaxContigs = 4096;
+static_assert(kMcChunk % kMcBlock == 0, "a chunk is staged in whole rounds of the block");
 // Resident CTAs per SM of the Monte-Carlo kernels: the shared-memory top and
 // staging (~45 KB a CTA) would allow five, but four with the shared-memory
 // carveout fitted to them leave ~60 KB of L1 for the level-0 chunk loads,
@@ -44,14 +45,26 @@ __device__ __forceinline__ int contig_of(const uint32_t* s_coff, uint32_t nc, ui
 // Stage intervals [i0, i0 + cn) of A: contig offset, length and number of
 // possible starts (contig length - length + 1).  An interval that is
 // inverted, lies before the first contig or crosses its contig's end sets
-// `bad` and is pinned in place (range 1, length 0).
+// `bad` and is pinned in place (range 1, length 0).  Each thread issues all
+// of its loads before it uses any, so a chunk costs one memory round trip.
+// Must be called by exactly kMcBlock threads.
 __device__ __forceinline__ void mc_stage_chunk(const uint2* __restrict__ A, uint32_t i0,
                                                uint32_t cn, const uint32_t* s_coff,
                                                const uint32_t* s_clen, uint32_t nc,
                                                uint32_t* s_off, uint32_t* s_len, uint32_t* s_rng,
                                                bool& bad) {
-  for (uint32_t k = threadIdx.x; k < cn; k += blockDim.x) {
-    const uint2 q = A[i0 + k];
+  constexpr int kPer = kMcChunk / kMcBlock;
+  uint2 qs[kPer];
+  #pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const uint32_t k = threadIdx.x + (uint32_t)r * kMcBlock;
+    qs[r] = k < cn ? A[i0 + k] : make_uint2(0u, 0u);
+  }
+  #pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const uint32_t k = threadIdx.x + (uint32_t)r * kMcBlock;
+    if (k >= cn) continue;
+    const uint2 q = qs[r];
     const int c = contig_of(s_coff, nc, q.x);
     const bool ok = c >= 0 && q.y >= q.x &&
                     (unsigned long long)q.y <= (unsigned long long)s_coff[c] + s_clen[c];

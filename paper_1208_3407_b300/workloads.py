@@ -12,6 +12,7 @@ Workloads (inputs from the seeded generator ``bits_synth``):
     allpairs-16x8    the same on the first 16 query sets and 8 databases
     mc-screen-64x32  bits_mc_matrix over those sets, 4 shuffles, with the summary
     mc-screen-16x8   the same on the first 16 query sets and 8 databases
+                     (--shuffles N: shuffles per call, default 4)
 
 Every call checks the device error word at the end; the script prints one
 line per workload with the device time of the last repetition.
@@ -53,6 +54,7 @@ def main(argv=None):
     ap.add_argument("name")
     ap.add_argument("--method", default="search", choices=sorted(METHODS))
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--shuffles", type=int, default=4, help="shuffles per Monte-Carlo screen call")
     args = ap.parse_args(argv)
     m = METHODS[args.method]
     ms = 0.0
@@ -110,11 +112,12 @@ def main(argv=None):
         dbs = [Database(_dev(b)) for b in b_sets]
         a = [_dev(x) for x in a_sets]
         dco, dcl = _dev(co), _dev(cl)
+        ns = args.shuffles
         out = (torch.empty((len(a), len(dbs)), dtype=torch.uint64, device="cuda"),
-               torch.empty((len(a), len(dbs), 4), dtype=torch.uint64, device="cuda"),
+               torch.empty((len(a), len(dbs), ns), dtype=torch.uint64, device="cuda"),
                torch.empty((len(a), len(dbs), 8), dtype=torch.uint64, device="cuda"))
         for _ in range(args.reps):
-            ms = _timed(lambda: mc_matrix(dbs, a, dco, dcl, seed=17, shuffle_end=4, out=out))
+            ms = _timed(lambda: mc_matrix(dbs, a, dco, dcl, seed=17, shuffle_end=ns, out=out))
         for d in dbs:
             d.check()
     else:
