@@ -20,7 +20,7 @@ constexpr size_t kTmpWords = kMaxN;               // one ping-pong buffer
 constexpr size_t kHistWords = kRadixHistWords;    // 2 arrays x 4 passes x 256 digits + flag
 constexpr size_t kTicketWords = 64;               // 2 x 4 used, padded to 256 B
 constexpr size_t kErrWords = 64;                  // 1 used, padded to 256 B
-constexpr size_t kStatusWords = ((kMaxN + 8191) / 8192) * 256 * 8;  // 2 arrays x 4 passes
+constexpr size_t kStatusWords = radix_status_words_max(kMaxN) * 8;  // 2 arrays x 4 passes
 
 constexpr size_t kOffTmpS = 0;
 constexpr size_t kOffTmpE = kOffTmpS + kTmpWords;

@@ -38,6 +38,7 @@ constexpr int kSwBlock = 512;
 constexpr int kSwWarps = kSwBlock / 32;
 constexpr int kSwKpt = 16;
 constexpr int kSwTile = kSwBlock * kSwKpt;  // 8192 keys
+static_assert(kSwTile == (int)kRadixTileKeys, "tile size shared with the look-back sizing");
 constexpr int kLookAhead = 8;  // predecessor status words read per round trip
 constexpr int kCnt = kRadix + 1;  // per-warp counters: 256 digits + the tail's empty lanes
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kValMask = (1u << 30) - 1;
@@ -334,10 +335,7 @@ void prepare_sweep() {
 
 }  // namespace
 
-size_t radix_status_words(uint32_t n) {
-  const uint32_t tiles = (n + kSwTile - 1) / kSwTile;
-  return (size_t)tiles * kRadix;
-}
+size_t radix_status_words(uint32_t n) { return radix_status_words_max(n); }
 
 bits_status radix_sort_pairs(const uint2* d_src, uint32_t n, const SortSpec spec[2], int validate,
                              uint32_t* d_err, RadixScratch& ws, cudaStream_t st,

@@ -16,6 +16,13 @@ struct RadixScratch {
 
 constexpr size_t kRadixHistWords = 2 * 4 * 256 + 64;
 
+// Keys a one-sweep tile holds (threads x keys per thread); the look-back
+// table has 256 words per tile, array and pass.
+constexpr uint32_t kRadixTileKeys = 8192;
+constexpr size_t radix_status_words_max(uint32_t n) {
+  return (size_t)((n + kRadixTileKeys - 1) / kRadixTileKeys) * 256;
+}
+
 // One of the two arrays a sort produces.  Its keys come from the interval
 // pairs: word `comp` (0 start, 1 end) plus `add`.  With out_vals set, the
 // values are the intervals' indices, top bit set for inverted intervals when
