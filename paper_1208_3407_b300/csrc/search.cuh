@@ -42,10 +42,6 @@ struct LevelIndex {
   int J;
 };
 
-__device__ __forceinline__ uint4 ldg4(const uint32_t* p) {
-  return __ldg(reinterpret_cast<const uint4*>(p));
-}
-
 // L2 cache policies for the tree levels.  The upper levels (1/16, 1/256, ...
 // of the array) are re-read by every search and should stay in L2; the
 // level-0 chunks are touched about once per search and should not push them
