@@ -424,7 +424,9 @@ def run_ours(args):
         def mc_step(m=m, res=res):
             res.append(db3.mc(a3, co, cl, seed=7, shuffle_end=n_sh, totals=totals3, method=m))
 
-        ms, l, _ = timed(mc_step, args.steps, args.warmup)
+        ms, l, win = timed(mc_step, args.steps, args.warmup)
+        if name == "search":
+            mc_window = win
         mc_forms[name] = {"ms_per_step": ms, "shuffles_per_s": world * n_sh / (ms * 1e-3),
                           "placements_per_s": world * n_sh * a3_np.shape[0] / (ms * 1e-3),
                           "gpu_launches": l}
@@ -440,15 +442,7 @@ def run_ours(args):
     mc_src = ["paper_1208_3407_b300/csrc/mc.cu", "paper_1208_3407_b300/csrc/mc_unit.cuh",
               "paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/philox.cuh"]
     wi = profiled_value("k_mc_search", "warp_instructions_per_launch", mc_src)
-    mc_roof = None
-    if wi is not None and clocks.get("sm_mhz"):
-        issue_peak = 148 * 4 * clocks["sm_mhz"] * 1e6
-        ach = wi / (mc_forms["search"]["ms_per_step"] * 1e-3)
-        mc_roof = {"bound": "alu", "achieved": ach, "peak": issue_peak,
-                   "unit": "warp-instructions/s", "frac": ach / issue_peak,
-                   "kernel": "k_mc_search<false>",
-                   "peak_source": "148 SMs x 4 schedulers x 1 warp-instruction/clock at the "
-                                  "sampled SM clock"}
+    mc_roof = None  # filled in once the clock samples of its timed window are in
     nodes_pp = 2 * tree_levels(b3_np.shape[0])
     mc_l2 = {"bound": "L2 random 64-B node reads", "kernel": "k_mc_search<false>",
              "achieved": nodes_pp * n_sh * a3_np.shape[0] / (mc_forms["search"]["ms_per_step"] * 1e-3),
@@ -568,7 +562,7 @@ def run_ours(args):
         bits.mc_matrix(dbs5, a5, dco5, dcl5, seed=17, shuffle_end=nsh5, out=scr_out)
 
     screen_step()                                  # builds and caches the launch graph
-    ms_scr, l_scr, _ = timed(screen_step, 3, 3)
+    ms_scr, l_scr, scr_window = timed(screen_step, 3, 3)
     for d in dbs5:
         d.check()
     i_s = int(np.argmin([x.shape[0] for x in a5_np]))
@@ -584,16 +578,7 @@ def run_ours(args):
               "paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/philox.cuh"]
     wi_m = profiled_value("k_mc_matrix_screen_16x8", "warp_instructions_per_launch", mm_src)
     pl_m = profiled_value("k_mc_matrix_screen_16x8", "placements_per_launch", mm_src)
-    scr_roof = None
-    if wi_m is not None and pl_m and clocks.get("sm_mhz"):
-        issue_peak = 148 * 4 * clocks["sm_mhz"] * 1e6
-        ach = wi_m / pl_m * placements / (ms_scr * 1e-3)
-        scr_roof = {"bound": "alu", "achieved": ach, "peak": issue_peak,
-                    "unit": "warp-instructions/s", "frac": ach / issue_peak,
-                    "kernel": "k_mc_matrix",
-                    "peak_source": "148 SMs x 4 schedulers x 1 warp-instruction/clock at the "
-                                   "sampled SM clock; instructions per placement from the "
-                                   "16 x 8 capture"}
+    scr_roof = None  # filled in once the clock samples of its timed window are in
     scr_nodes = sum(x.shape[0] * nsh5 * 2 * tree_levels(b5.shape[0])
                     for x in a5_np for b5 in b5_np)
     scr_l2 = {"bound": "L2 random 64-B node reads", "kernel": "k_mc_matrix",
@@ -617,6 +602,29 @@ def run_ours(args):
     del a5, m5, scr_out
 
     sampler.stop()
+
+    # Instruction-issue rooflines of the Monte-Carlo kernels, at the SM clock
+    # sampled during their own timed windows (long, busy phases of the run,
+    # unlike the microsecond headline steps).
+    def issue_roofline(warp_instr, ms, window, kernel, note):
+        ck = sampler.summary(*window)
+        mhz = ck.get("sm_mhz") or clocks.get("sm_mhz")
+        if warp_instr is None or not mhz:
+            return None
+        peak = 148 * 4 * mhz * 1e6
+        ach = warp_instr / (ms * 1e-3)
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "warp-instructions/s",
+                "frac": ach / peak, "kernel": kernel, "clocks": ck,
+                "peak_source": "148 SMs x 4 schedulers x 1 warp-instruction/clock at the SM "
+                               "clock sampled during this workload's timed steps" + note}
+
+    mc["roofline"] = issue_roofline(wi, mc_forms["search"]["ms_per_step"], mc_window,
+                                    "k_mc_search<false>", "")
+    if wi_m is not None and pl_m:
+        mc_screen["roofline"] = issue_roofline(wi_m / pl_m * placements, ms_scr, scr_window,
+                                               "k_mc_matrix",
+                                               "; instructions per placement from the 16 x 8 "
+                                               "capture")
 
     # ---- CPU baseline: the oracle as it stands, on a bounded sample -----------
     cpu = None
