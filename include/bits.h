@@ -84,6 +84,10 @@ typedef struct bits_opts {
  *   n     number of database intervals, 0 <= n < 2^30 (else BITS_EOVERFLOW).
  *   out   receives the new database handle (owns B_S, B_E, search tree and
  *         the optional learned index).
+ * Device memory per database: about 16.5 bytes per interval (B_S and B_E,
+ * their levels stored once more with node i of both arrays in one 128-byte
+ * line for the searches, and the upper levels), plus 64 bytes per pair of
+ * learned-index leaves and 8 bytes per interval with BITS_FLAG_ENUMERATE.
  * Sorting is the library's own LSD radix sort.  The call synchronises the
  * stream once (it reads the validation flag): BITS_EINVAL if any interval has
  * end <= start, in which case *out is left NULL.
