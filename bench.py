@@ -297,6 +297,19 @@ def run_ours(args):
         db_tmp.free()
     build_ms = max_over_ranks(sum(x for x, _ in build_list) / len(build_list))
     build_launches = build_list[-1][1]
+
+    # One-shot form of the same workload (the paper's single intersection,
+    # Fig. 2: setup + count): build the database from the 20M reads, count
+    # the 200k queries, free it -- per step.
+    one_counts = torch.empty(n_a, dtype=torch.uint32, device=dev)
+    one_total = torch.empty(1, dtype=torch.uint64, device=dev)
+
+    def one_shot_step():
+        d = bits.Database(b)
+        d.count(a, counts=one_counts, total=one_total, method=bits.METHOD_SEARCH, check=False)
+        d.free()
+
+    one_ms, one_launches, _ = timed(one_shot_step, args.steps, args.warmup)
     t_rmi = time.time()
     db = bits.Database(b, rmi_leaves_log2=16)          # plain levels + learned index
     torch.cuda.synchronize()
@@ -691,6 +704,10 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "forms": forms,
+        "one_shot": {"ms_per_step": one_ms, "queries_per_s": world * n_a / (one_ms * 1e-3),
+                     "gpu_launches": one_launches,
+                     "call": "bits_build_db of the 20M reads (radix sort of B_S and B_E, tree "
+                             "levels) + bits_count of the 200k queries + bits_free, per step"},
         "build": {"ms": build_ms, "intervals": n_b, "intervals_per_s": n_b / (build_ms * 1e-3),
                   "gpu_launches": build_launches,
                   "with_learned_index_s": build_rmi_s},
