@@ -5,6 +5,8 @@ bounds, fitted on the device) is not in the paper; it replaces the first
 steps of each BSearch of Algorithm 1.  Its counts must equal the oracle's and
 the plain search's bit for bit, including when its error bounds are wrong.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -140,7 +142,9 @@ def test_mc_learned_index_equals_plain_and_oracle(bits):
 
 def test_config4_full_size_learned_vs_plain(bits):
     """100M queries vs 100M intervals, 2^16 leaves: both forms bit-exact with
-    each other; the oracle recomputes 64 sampled queries by brute force."""
+    each other and with the oracle's count of every query (std::sort and
+    std::lower_bound on the host, all cores); 64 sampled queries are also
+    recomputed by brute force."""
     a, b = synth.config4()
     db = bits.Database(dev(b), rmi_leaves_log2=16)
     da = dev(a)
@@ -154,7 +158,12 @@ def test_config4_full_size_learned_vs_plain(bits):
         x64 = x.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
         assert bool((x64[1:] >= x64[:-1]).all())
         del x64
+    got = c_r.cpu().numpy()
+    obs, obe = O.build(b)
+    oc_all, ot_all = O.count_sorted(a, obs, obe, threads=os.cpu_count() or 1)
+    np.testing.assert_array_equal(got, oc_all)
+    assert ot_all == total
     idx = np.random.default_rng(1).choice(a.shape[0], size=64, replace=False)
     oc, _ = O.count_brute(a[idx], b)
-    np.testing.assert_array_equal(c_r.cpu().numpy()[idx], oc)
+    np.testing.assert_array_equal(got[idx], oc)
     db.free()
