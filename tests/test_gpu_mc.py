@@ -3,6 +3,8 @@
 Per-shuffle totals, the observed total, k_ge and the p-value must match the
 oracle bit-exactly on the same seeded inputs and the same Philox counters.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -112,7 +114,9 @@ def test_interval_crossing_contig_is_rejected(bits):
 
 def test_config3_full_size_sampled_shuffles(bits):
     """10,000 shuffles of 100k intervals vs 1M in one launch; the oracle
-    recomputes 24 of them one by one, the observed total and the tally."""
+    recomputes the first block of 256 shuffles, the last 272 (a full block
+    and the short block of 16 that the kernel splits between thread
+    groups), 24 spread over the rest, the observed total and the tally."""
     genome, a, b = synth.config3()
     co, cl = synth.mc_contig_table(genome)
     db = bits.Database(dev(b))
@@ -127,3 +131,7 @@ def test_config3_full_size_sampled_shuffles(bits):
     for s in np.linspace(0, 9999, 24).astype(int):
         ot, *_ = O.mc(a, co, cl, bs, be, seed=7, s_begin=int(s), s_end=int(s) + 1)
         assert t[s] == ot[0], s
+    cores = os.cpu_count() or 1
+    for lo, hi in ((0, 256), (9728, 10_000)):
+        ot, *_ = O.mc(a, co, cl, bs, be, seed=7, s_begin=lo, s_end=hi, threads=cores)
+        np.testing.assert_array_equal(t[lo:hi], ot)
