@@ -127,10 +127,11 @@ bits_status bits_count_method(const bits_db* db, int32_t method, const uint32_t*
  * nothing is staged.  Pageable buffers are staged through stream-ordered
  * device memory with cudaMemcpyAsync; merge path always stages.  The total
  * is added up in a stream-ordered device word of the call's own and copied
- * to h_total.  That memory comes from the library's temporary pool.  Stream-ordered like every call: with
- * page-locked buffers it returns at once and the results are in place when
- * `stream` has been synchronised; a pageable h_total or h_counts makes the
- * call wait for its copy, as cudaMemcpyAsync does.  Inverted queries count
+ * to h_total; that memory comes from the library's pool.  Stream-ordered
+ * like every call: with page-locked buffers it returns at once and the
+ * results are in place when `stream` has been synchronised; a pageable
+ * h_total or h_counts makes the call wait for its copy, as cudaMemcpyAsync
+ * does.  Inverted queries count
  * 0 and set the database's device error word (bits_check).  BITS_EINVAL if a
  * buffer is device memory or the database belongs to another device than
  * the current one.

@@ -9,7 +9,7 @@
 // through a stream-ordered device buffer with cudaMemcpyAsync.  The 64-bit
 // total is added up in a stream-ordered device word of its own per call
 // (so calls on different streams do not share it) and copied back.  Both
-// come from the library's scratch pool.
+// come from the library's stream-ordered memory pool (pool_alloc).
 
 #include "count.cuh"
 #include "db.cuh"

@@ -4,8 +4,10 @@
 // Every search kernel here reads one 64-byte node per level of the 16-ary
 // tree, loaded by a quad of lanes (16 bytes each) with a 64-byte line fill.
 // On a database much larger than L2 the level-0 nodes come from DRAM at
-// random, and the rate of such reads, not the byte bandwidth, bounds the
-// kernels: random 64-byte reads reach about a third of the copy bandwidth.
+// random, and the rate of such reads, not the byte bandwidth, limits the
+// kernels: independent random 64-byte reads over a buffer far beyond L2
+// reach about a third of the copy bandwidth (the tree's interleaved node
+// pairs let the counts go somewhat beyond that rate).
 // This probe issues exactly that access -- quads reading uniformly random
 // nodes of a buffer, four independent accesses in flight per quad -- and
 // times it with CUDA events, so the search kernels can be set against the
