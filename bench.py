@@ -7,11 +7,14 @@ Headline workload (one "step"): bits_count of the exome-vs-reads shape --
 uint32 counts plus the uint64 total.  L2 is flushed before every timed step.
 
 Also reported on the same line: the database build (radix sort of B_S and
-B_E), the learned-index and merge-path forms of the same count, the
-Monte-Carlo test (100,000 intervals vs 1,000,000, 10,000 shuffles per
-launch), the learned-index count at 100M x 100M, an end-to-end number
-through the public API with host buffers, and the CPU oracle timed on this
-host's cores.
+B_E) and the one-shot form (build + count per step), the learned-index and
+merge-path forms of the same count, the count end to end through the C ABI
+with host buffers (bits_count_host), the projection and the enumeration of
+the same workload, the Monte-Carlo test (100,000 intervals vs 1,000,000,
+10,000 shuffles per launch), the 100M x 100M count in every form, the 64 x
+32 all-pairs count and Monte-Carlo screen, the random-read rates these
+kernels are set against (bits_probe_random_reads, DRAM and L2), and the CPU
+oracle timed on this host's cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
