@@ -91,3 +91,38 @@ def read_enumerate_fixture():
             if line and line[0] == "E":
                 partners[int(line[1])] = [int(x) for x in line[2:]]
     return a, b, exp, total, [partners[i] for i in range(a.shape[0])]
+
+
+def read_mc_fullsize():
+    """Full-size Monte-Carlo expected values (make_fullsize.py): returns
+    (observed, k_ge, (p numerator, p denominator), totals uint64[10000])."""
+    obs = k = p = None
+    totals = []
+    with open(os.path.join(GOLDEN, "mc_100k_1m_10000.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if not line:
+                continue
+            if line[0] == "OBSERVED":
+                obs = int(line[1])
+            elif line[0] == "K_GE":
+                k = int(line[1])
+            elif line[0] == "P":
+                num, den = line[1].split("/")
+                p = (int(num), int(den))
+            else:
+                assert int(line[0]) == len(totals)
+                totals.append(int(line[1]))
+    return obs, k, p, np.array(totals, np.uint64)
+
+
+def read_allpairs_fullsize():
+    """Full-size all-pairs expected matrix (make_fullsize.py): uint64[64, 32]."""
+    rows = []
+    with open(os.path.join(GOLDEN, "allpairs_64x32.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                assert int(line[0]) == len(rows)
+                rows.append([int(x) for x in line[1:]])
+    return np.array(rows, np.uint64)

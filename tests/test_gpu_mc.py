@@ -1,15 +1,14 @@
-"""Parity of the Monte-Carlo significance test (Sec. 3.2) with the CPU oracle.
+"""Parity of the Monte-Carlo significance test (Sec. "Monte Carlo Simulations") with the CPU oracle.
 
 Per-shuffle totals, the observed total, k_ge and the p-value must match the
 oracle bit-exactly on the same seeded inputs and the same Philox counters.
 """
-import os
-
 import numpy as np
 import pytest
 import torch
 
 import bits_synth as synth
+import goldens
 import oracle
 
 pytestmark = pytest.mark.gpu
@@ -112,26 +111,21 @@ def test_interval_crossing_contig_is_rejected(bits):
     db.free()
 
 
-def test_config3_full_size_sampled_shuffles(bits):
-    """10,000 shuffles of 100k intervals vs 1M in one launch; the oracle
-    recomputes the first block of 256 shuffles, the last 272 (a full block
-    and the short block of 16 that the kernel splits between thread
-    groups), 24 spread over the rest, the observed total and the tally."""
+@pytest.mark.parametrize("method", ["search", "rmi"])
+def test_config3_full_size_every_shuffle(bits, method):
+    """Table 1's 1e5 x 1e4 corner at full size: 10,000 shuffles of 100,000
+    intervals against 1,000,000 in one launch.  Every per-shuffle total, the
+    observed total, k_ge and the p-value equal the oracle's, which
+    tests/golden/make_fullsize.py wrote from the oracle alone (the full run
+    takes about a minute on eight host cores)."""
+    gobs, gk, (pnum, pden), gtot = goldens.read_mc_fullsize()
     genome, a, b = synth.config3()
     co, cl = synth.mc_contig_table(genome)
-    db = bits.Database(dev(b))
-    totals, obs, k, p = db.mc(dev(a), dev(co), dev(cl), seed=7, shuffle_end=10_000,
-                              method=bits.METHOD_SEARCH)
+    db = bits.Database(dev(b), rmi_leaves_log2=16 if method == "rmi" else 0)
+    m = bits.METHOD_RMI if method == "rmi" else bits.METHOD_SEARCH
+    totals, obs, k, p = db.mc(dev(a), dev(co), dev(cl), seed=7, shuffle_end=10_000, method=m)
     t = totals.cpu().numpy()
     db.free()
-    bs, be = O.build(b)
-    _, oobs = O.count_sorted(a, bs, be, threads=8, want_counts=False)
-    assert obs == oobs
-    assert k == int((t >= obs).sum()) and p == (k + 1) / 10_001
-    for s in np.linspace(0, 9999, 24).astype(int):
-        ot, *_ = O.mc(a, co, cl, bs, be, seed=7, s_begin=int(s), s_end=int(s) + 1)
-        assert t[s] == ot[0], s
-    cores = os.cpu_count() or 1
-    for lo, hi in ((0, 256), (9728, 10_000)):
-        ot, *_ = O.mc(a, co, cl, bs, be, seed=7, s_begin=lo, s_end=hi, threads=cores)
-        np.testing.assert_array_equal(t[lo:hi], ot)
+    np.testing.assert_array_equal(t, gtot)
+    assert (obs, k) == (gobs, gk)
+    assert p == pnum / pden
