@@ -7,15 +7,17 @@
  * arrays B_S and B_E, the number of database intervals meeting a is
  *     ICount(a) = #(B_S < a.end) - #(B_E <= a.start)           (Algorithm 1)
  * which equals |B| minus the intervals wholly right of a, minus those wholly
- * left of a (Sec. 2.2, the sets L and R).  The counting problem sums ICount
- * over A (Algorithm 2); the Monte-Carlo significance test (Sec. 3.2) recounts
- * after re-placing A at random many times.
+ * left of a (Sec. "BITS Algorithm", the sets L and R).  The counting problem
+ * sums ICount over A (Algorithm 2); the Monte-Carlo significance test (Sec.
+ * "Monte Carlo Simulations") recounts after re-placing A at random many
+ * times.  Passages are cited by the title of their subsection.
  *
  * Conventions shared by every call:
  *   - Intervals are half-open [start, end) pairs of uint32 on one genome-wide
  *     coordinate line (contigs already projected by adding their offsets, as
- *     Sec. 2.3 describes).  An interval set is an array of structures: element
- *     i is the two consecutive words (start_i, end_i), 8 bytes per interval.
+ *     the projection paragraph of Sec. "BITS Algorithm" describes).  An
+ *     interval set is an array of structures: element i is the two
+ *     consecutive words (start_i, end_i), 8 bytes per interval.
  *     a and b intersect iff b.start < a.end and b.end > a.start.
  *   - Database intervals must be non-empty (start < end).  Queries may be
  *     empty (start == end) and then count the database intervals with
@@ -53,7 +55,9 @@ typedef enum bits_status {
   BITS_ECUDA = 3,      /* CUDA runtime error (message in bits_last_error)        */
   BITS_EOVERFLOW = 4,  /* a size beyond the supported range                      */
   BITS_ETIMEOUT = 5,   /* a bounded device-side wait gave up; results invalid    */
-  BITS_ENOTIMPL = 6    /* method not built into this database                    */
+  BITS_ENOTIMPL = 6,   /* method not built into this database                    */
+  BITS_EINTERNAL = 7   /* a device-side consistency check failed (a library bug,  */
+                       /* e.g. a sort scatter index out of range); results invalid */
 } bits_status;
 
 typedef enum bits_method {
@@ -140,8 +144,9 @@ bits_status bits_count_host(const bits_db* db, int32_t method, const uint32_t* h
                             uint32_t* h_counts, uint64_t* h_total, void* stream);
 
 /*
- * Enumeration problem (Sec. 1.1: report every intersecting pair), in two
- * stream-ordered steps so that the caller can size the output in between.
+ * Enumeration problem (Sec. "Interval Set Intersection problem": report every
+ * intersecting pair), in two stream-ordered steps so that the caller can size
+ * the output in between.
  *
  * bits_enumerate_offsets -- d_offsets (device uint64[n + 1]) receives the
  * exclusive prefix sum of ICount over the queries: query i's pairs occupy
@@ -152,10 +157,11 @@ bits_status bits_count_host(const bits_db* db, int32_t method, const uint32_t* h
  * interval index) uint32 pairs in d_pairs (device, 8-byte aligned,
  * d_offsets[n] pairs), given the offsets of the same queries and database.
  * Needs a database built with BITS_FLAG_ENUMERATE (else BITS_ENOTIMPL).  As
- * Sec. 2.2 suggests, ICount ends the scan: the database intervals in start
- * order left of first = #(B_S < a.end) are walked right to left and those
- * with end > a.start kept until the count is reached, so a query's pairs
- * come in descending start order (equal starts: descending index).  A query
+ * Sec. "BITS Algorithm" suggests, ICount ends the scan: the database
+ * intervals in start order left of first = #(B_S < a.end) are walked right to
+ * left and those with end > a.start kept until the count is reached, so a
+ * query's pairs come in descending start order (equal starts: descending
+ * index).  A query
  * under a long interval that contains many others scans past them (the
  * paper's containment case).  Asynchronous; offsets that do not match the
  * queries set the device error word (bits_check: BITS_EINVAL).
@@ -166,10 +172,10 @@ bits_status bits_enumerate_pairs(const bits_db* db, const uint32_t* d_a, uint64_
                                  const uint64_t* d_offsets, uint32_t* d_pairs, void* stream);
 
 /*
- * bits_mc -- Monte-Carlo significance test of Sec. 3.2.  Each shuffle s in
- * [shuffle_begin, shuffle_end) re-places every query interval uniformly inside
- * its own contig with its length kept, and recounts it against the fixed
- * database.  Interval i of shuffle s draws Philox4x32-10 with counter
+ * bits_mc -- Monte-Carlo significance test of Sec. "Monte Carlo
+ * Simulations".  Each shuffle s in [shuffle_begin, shuffle_end) re-places
+ * every query interval uniformly inside its own contig with its length kept,
+ * and recounts it against the fixed database.  Interval i of shuffle s draws Philox4x32-10 with counter
  * (i, s, 0, 0) and key (seed & 0xffffffff, seed >> 32); with u = x1*2^32 + x0
  * its new start is off[c] + floor(u * (len[c] - len_i + 1) / 2^64).
  *   d_contig_off, d_contig_len  device uint32[n_contigs], the contig table on
@@ -214,7 +220,8 @@ typedef struct bits_mc_stat {
 
 /*
  * bits_mc_summary -- bits_mc_stat of n_tests Monte-Carlo tests at once (the
- * Sec. 3.2 tally in both directions and the Fig. 3 score).
+ * tally of Sec. "Monte Carlo Simulations" in both directions and the Fig. 3
+ * score).
  *   d_totals    device uint64[n_tests][n_shuffles], row t = test t's totals.
  *   d_observed  device uint64[n_tests].
  *   d_stats     device bits_mc_stat[n_tests], 8-byte aligned.
@@ -225,8 +232,9 @@ bits_status bits_mc_summary(const uint64_t* d_totals, uint32_t n_shuffles, uint3
                             const uint64_t* d_observed, bits_mc_stat* d_stats, void* stream);
 
 /*
- * bits_mc_matrix -- the Monte-Carlo screen of Sec. 3.3: a significance test
- * (Sec. 3.2) for every pair of query set A_i and database B_j.
+ * bits_mc_matrix -- the Monte-Carlo screen of Sec. "Novel genomic
+ * relationships": a significance test (Sec. "Monte Carlo Simulations") for
+ * every pair of query set A_i and database B_j.
  *   dbs, n_db, d_as, n_as, n_sets   as bits_count_matrix.
  *   d_contig_off, d_contig_len, n_contigs, seed, shuffle_begin, shuffle_end
  *                as bits_mc; one contig table for every set (n_contigs <= 4096).
@@ -249,7 +257,8 @@ bits_status bits_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint3
                            uint64_t* d_totals, bits_mc_stat* d_stats, void* stream);
 
 /*
- * bits_count_matrix -- all-pairs screen of Sec. 3.3: M[i][j] = total(A_i, B_j).
+ * bits_count_matrix -- all-pairs screen of Sec. "Novel genomic relationships":
+ * M[i][j] = total(A_i, B_j).
  *   dbs      host array of n_db database handles (all on this device).
  *   d_as     host array of n_sets device pointers to query sets.
  *   n_as     host array of n_sets query-set sizes.
@@ -262,12 +271,13 @@ bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
                               uint64_t* d_matrix, void* stream);
 
 /*
- * bits_project -- the mapping of Sec. 2.3 that places every chromosome after
- * the previous ones on one genome-wide line, and the conversion of closed
- * intervals (Sec. 1.1 states its predicate for closed [start, end]) to the
- * half-open form every other call takes: [s, e] on the integers is
- * [s, e + 1).  Interval i on chromosome c = d_contig[i] becomes
- * [off[c] + start_i, off[c] + end_i), plus one on the end when closed.
+ * bits_project -- the mapping of Sec. "BITS Algorithm" (projection) that
+ * places every chromosome after the previous ones on one genome-wide line, and
+ * the conversion of closed intervals (Sec. "Interval Set Intersection problem"
+ * states its predicate for closed [start, end]) to the half-open form every
+ * other call takes: [s, e] on the integers is [s, e + 1).  Interval i on
+ * chromosome c = d_contig[i] becomes [off[c] + start_i, off[c] + end_i), plus
+ * one on the end when closed.
  *   d_contig      device uint32[n], chromosome ids; ignored (may be NULL) when
  *                 n_contigs == 0, which means one line at offset 0 with
  *                 length 2^32 - 1.
@@ -306,8 +316,11 @@ bits_status bits_project(const uint32_t* d_contig, const uint32_t* d_start, cons
  * (cudaGetSymbolAddress), so make that first call before any stream capture.
  * All calls on a device share the one scratch array: calls that overlap on
  * the GPU (other streams, other host threads) race and must be serialised
- * by the caller.  Synchronises `stream`; BITS_EINVAL if an interval has
- * end <= start.
+ * by the caller.  The call synchronises `stream` (it reads the sort's digit
+ * histograms and its error word back).  BITS_EINVAL if an interval has
+ * end <= start; the error word is cleared at the start of every call, so a
+ * later valid call succeeds.  BITS_EINTERNAL if the sort's own consistency
+ * check fails (a library bug).
  */
 #define BITS_NOALLOC_MAX_INTERVALS 262144u
 bits_status bits_sort_intervals_noalloc(const uint32_t* d_b, uint64_t n, uint32_t* d_bs,
@@ -323,31 +336,6 @@ bits_status bits_sort_intervals_noalloc(const uint32_t* d_b, uint64_t n, uint32_
  * context stays usable.  Synchronises `stream`.
  */
 bits_status bits_selftest_wait(uint32_t spin_limit, void* stream);
-
-/*
- * bits_probe_random_reads -- diagnostic (not in the paper): the rate at
- * which this GPU serves random 64-byte node reads, the access every search
- * kernel makes once per tree level; on a database much larger than L2 the
- * level-0 reads come from DRAM and this rate bounds the counting kernels.
- * Quads of lanes make uniformly random accesses to d_buf with a 64-byte line
- * fill, four accesses in flight per quad, timed with CUDA events.
- *   d_buf             device buffer, aligned to one access, `bytes` long
- *                     (contents are read, not used); much larger than L2
- *                     (e.g. 4 GiB) for the DRAM rate, well inside it (e.g.
- *                     32 MiB) for the L2 rate.
- *   bytes             a multiple of the access size, at most 2^32 - 1 accesses.
- *   n_reads           accesses to make, 1 .. 2^34 (rounded up to whole rounds
- *                     of the grid).
- *   nodes_per_access  1: one 64-byte node per access; 2: both 64-byte halves
- *                     of one random 128-byte line, read as two node loads (a
- *                     query whose start and end searches meet in one
- *                     interleaved node pair).
- *   h_accesses_per_s  host double receiving the accesses per second.
- * Synchronises `stream`.
- */
-bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes, uint64_t n_reads,
-                                    int32_t nodes_per_access, double* h_accesses_per_s,
-                                    void* stream);
 
 /* Read-only views of the database (sorted starts, sorted ends, size). */
 bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_t** d_be,

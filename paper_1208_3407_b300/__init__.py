@@ -20,7 +20,7 @@ from ._lib import (METHOD_AUTO, METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, Bit
                    LIB_PATH)
 
 __all__ = ["Database", "count_matrix", "project", "mc_summary", "mc_matrix", "McStats",
-           "kernel_launches", "probe_random_reads", "BitsError", "METHOD_AUTO",
+           "kernel_launches", "BitsError", "METHOD_AUTO",
            "METHOD_SEARCH", "METHOD_RMI", "METHOD_MERGEPATH", "LIB_PATH", "device_view"]
 
 _U32 = (torch.uint32, torch.int32)
@@ -176,7 +176,8 @@ class Database:
         return out, (tot.value if total is None else total)
 
     def enumerate(self, a: torch.Tensor, *, stream=None, check: bool = True):
-        """Every intersecting pair (Sec. 1.1's enumeration problem).
+        """Every intersecting pair (the enumeration problem of Sec. "Interval
+        Set Intersection problem").
 
         Returns ``(offsets, pairs)``: uint64 offsets of shape ``(n + 1,)`` (query
         i's pairs are ``pairs[offsets[i]:offsets[i + 1]]``) and uint32 pairs of
@@ -210,7 +211,8 @@ class Database:
     def mc(self, a: torch.Tensor, contig_off: torch.Tensor, contig_len: torch.Tensor, *, seed: int,
            shuffle_begin: int = 0, shuffle_end: int, method: int = METHOD_AUTO,
            totals: torch.Tensor | None = None, stream=None):
-        """Monte-Carlo test (Sec. 3.2): (totals, observed, k_ge, p-value)."""
+        """Monte-Carlo test (Sec. "Monte Carlo Simulations"): (totals, observed,
+        k_ge, p-value)."""
         a = _intervals(a, "a")
         co = _u32_vec(contig_off, "contig_off")
         cl = _u32_vec(contig_len, "contig_len")
@@ -261,9 +263,10 @@ def project(start: torch.Tensor, end: torch.Tensor, *, contig: torch.Tensor | No
             contig_off: torch.Tensor | None = None, contig_len: torch.Tensor | None = None,
             closed: bool = False, out: torch.Tensor | None = None, stream=None):
     """Map chromosome-local (optionally closed) intervals onto the half-open
-    genome-wide line (Sec. 2.3).  Returns ``(intervals (n, 2) uint32, n_rejected)``
-    where ``n_rejected`` is a 1-element uint64 device tensor; rejected rows are
-    ``(2^32 - 1, 0)``.  Without a contig table the line is one contig at 0."""
+    genome-wide line (Sec. "BITS Algorithm" (projection)).  Returns
+    ``(intervals (n, 2) uint32, n_rejected)`` where ``n_rejected`` is a
+    1-element uint64 device tensor; rejected rows are ``(2^32 - 1, 0)``.
+    Without a contig table the line is one contig at 0."""
     lib = _lib.load()
     s = _u32_vec(start, "start")
     e = _u32_vec(end, "end")
@@ -357,7 +360,8 @@ def mc_summary(totals: torch.Tensor, observed: torch.Tensor, *, stream=None) -> 
 
 def mc_matrix(dbs, a_sets, contig_off: torch.Tensor, contig_len: torch.Tensor, *, seed: int,
               shuffle_begin: int = 0, shuffle_end: int, stats: bool = True, out=None, stream=None):
-    """Monte-Carlo screen (Sec. 3.3): (observed [S, D], totals [S, D, N], McStats or None).
+    """Monte-Carlo screen (Sec. "Novel genomic relationships"): (observed
+    [S, D], totals [S, D, N], McStats or None).
 
     ``out`` may pass the three output tensors (observed, totals, raw stats or
     None) to reuse; the launch graph is cached per output address."""
@@ -396,23 +400,6 @@ def mc_matrix(dbs, a_sets, contig_off: torch.Tensor, contig_len: torch.Tensor, *
                             _stream_ptr(stream))
     _lib.check(st, "bits_mc_matrix")
     return observed, totals, (McStats(raw) if raw is not None else None)
-
-
-def probe_random_reads(nbytes: int = 4 << 30, n_reads: int = 1 << 24, *, pairs: bool = False,
-                       device=None, stream=None) -> float:
-    """bits_probe_random_reads on a fresh ``nbytes`` device buffer: random
-    accesses per second, each one 64-byte node (or, with ``pairs``, both
-    halves of one 128-byte line) -- the bound of the search kernels on a
-    database much larger than L2."""
-    buf = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
-    rate = C.c_double()
-    with torch.cuda.device(buf.device):
-        _lib.check(_lib.load().bits_probe_random_reads(buf.data_ptr(), nbytes, n_reads,
-                                                       2 if pairs else 1, C.byref(rate),
-                                                       _stream_ptr(stream)),
-                   "bits_probe_random_reads")
-    del buf
-    return rate.value
 
 
 def kernel_launches() -> int:

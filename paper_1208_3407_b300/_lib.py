@@ -11,9 +11,10 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbits_b300.so")
 
-BITS_OK, BITS_EINVAL, BITS_ENOMEM, BITS_ECUDA, BITS_EOVERFLOW, BITS_ETIMEOUT, BITS_ENOTIMPL = range(7)
+(BITS_OK, BITS_EINVAL, BITS_ENOMEM, BITS_ECUDA, BITS_EOVERFLOW, BITS_ETIMEOUT, BITS_ENOTIMPL,
+ BITS_EINTERNAL) = range(8)
 STATUS_NAMES = {0: "BITS_OK", 1: "BITS_EINVAL", 2: "BITS_ENOMEM", 3: "BITS_ECUDA",
-                4: "BITS_EOVERFLOW", 5: "BITS_ETIMEOUT", 6: "BITS_ENOTIMPL"}
+                4: "BITS_EOVERFLOW", 5: "BITS_ETIMEOUT", 6: "BITS_ENOTIMPL", 7: "BITS_EINTERNAL"}
 
 METHOD_AUTO, METHOD_SEARCH, METHOD_RMI, METHOD_MERGEPATH = range(4)
 
@@ -21,8 +22,7 @@ METHOD_AUTO, METHOD_SEARCH, METHOD_RMI, METHOD_MERGEPATH = range(4)
 EXPORTS = ["bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc",
            "bits_count_matrix", "bits_db_info", "bits_check", "bits_free", "bits_last_error", "bits_kernel_launches",
            "bits_sort_intervals_noalloc", "bits_db_rmi", "bits_selftest_wait", "bits_project",
-           "bits_mc_summary", "bits_mc_matrix", "bits_enumerate_offsets", "bits_enumerate_pairs",
-           "bits_probe_random_reads"]
+           "bits_mc_summary", "bits_mc_matrix", "bits_enumerate_offsets", "bits_enumerate_pairs"]
 
 
 class BitsError(RuntimeError):
@@ -66,8 +66,6 @@ def load():
     lib.bits_check.argtypes = [vp, vp]
     lib.bits_sort_intervals_noalloc.argtypes = [u32p, C.c_uint64, u32p, u32p, vp]
     lib.bits_selftest_wait.argtypes = [C.c_uint32, vp]
-    lib.bits_probe_random_reads.argtypes = [vp, C.c_uint64, C.c_uint64, C.c_int32,
-                                            C.POINTER(C.c_double), vp]
     lib.bits_enumerate_offsets.argtypes = [vp, u32p, C.c_uint64, u64p, vp]
     lib.bits_enumerate_pairs.argtypes = [vp, u32p, C.c_uint64, u64p, u32p, vp]
     lib.bits_mc_summary.argtypes = [u64p, C.c_uint32, C.c_uint32, u64p, vp, vp]
@@ -81,7 +79,7 @@ def load():
     for f in ("bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc",
               "bits_count_matrix", "bits_db_info", "bits_check", "bits_sort_intervals_noalloc", "bits_db_rmi",
               "bits_selftest_wait", "bits_project", "bits_mc_summary", "bits_mc_matrix",
-              "bits_enumerate_offsets", "bits_enumerate_pairs", "bits_probe_random_reads"):
+              "bits_enumerate_offsets", "bits_enumerate_pairs"):
         getattr(lib, f).restype = st
     lib.bits_free.argtypes = [vp]
     lib.bits_free.restype = None

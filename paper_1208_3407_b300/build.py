@@ -1,4 +1,6 @@
-"""Compile the CUDA library (csrc/*.cu) for sm_103a into libbits_b300.so.
+"""Compile the CUDA library (csrc/*.cu) for sm_103a into libbits_b300.so,
+and the random-read probe (csrc/probe.cu, a measurement aid) into
+libbits_probe.so beside it.
 
 Run as ``python -m paper_1208_3407_b300.build`` or through
 ``__graft_entry__.build()``.  Objects go to ``_build/`` next to this file;
@@ -18,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbits_b300.so")
+LIB_PROBE = os.path.join(HERE, "libbits_probe.so")
+PROBE_OBJS = {"probe.o"}  # measurement aid, linked into LIB_PROBE only
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -49,6 +53,16 @@ def _compile(src: str) -> tuple[str, str]:
     return obj, r.stderr
 
 
+def _link(out: str, objs: list[str], extra: list[str]) -> None:
+    deps = objs + [x for x in extra if x.endswith(".so")]
+    if os.path.exists(out) and all(os.path.getmtime(o) <= os.path.getmtime(out) for o in deps):
+        return
+    cmd = [NVCC, *ARCH, "-shared", "-o", out, *objs, *[x for x in extra if not x.endswith(".so")]]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link of {out} failed:\n{r.stdout}\n{r.stderr}")
+
+
 def build(verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
@@ -57,14 +71,15 @@ def build(verbose: bool = False) -> str:
     with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
         for p in sorted(glob.glob(os.path.join(BUILD, "*.ptxas"))):
             f.write(open(p).read())
-    objs = [o for o, _ in results]
-    if (not os.path.exists(LIB)) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    objs = [o for o, _ in results if os.path.basename(o) not in PROBE_OBJS]
+    probe_objs = [o for o, _ in results if os.path.basename(o) in PROBE_OBJS]
+    _link(LIB, objs, [])
+    # The measurement probe is a library of its own that resolves the error
+    # reporting helpers from libbits_b300.so next to it.
+    _link(LIB_PROBE, probe_objs, [LIB, f"-L{HERE}", "-lbits_b300", "-Xlinker", "-rpath,$ORIGIN"])
     if verbose:
         print(LIB)
+        print(LIB_PROBE)
     return LIB
 
 

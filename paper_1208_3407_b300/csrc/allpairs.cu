@@ -1,5 +1,6 @@
-// All-pairs count matrix (the screen of Sec. 3.3): M[i][j] = total(A_i, B_j)
-// for every query set A_i and database B_j, in one persistent launch.
+// All-pairs count matrix (the screen of Sec. "Novel genomic relationships"):
+// M[i][j] = total(A_i, B_j) for every query set A_i and database B_j, in one
+// persistent launch.
 //
 // Work is split by query count: a unit is (database j, query set i, chunk of
 // kChunk queries), and units are listed database by database, largest
@@ -109,16 +110,7 @@ k_allpairs(MatArgs P) {
 }
 
 int ap_blocks_per_sm(size_t smem) {
-  static int per_sm = 0;
-  static size_t smem_for = 0;
-  if (per_sm == 0 || smem_for != smem) {
-    cudaFuncSetAttribute(k_allpairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_allpairs, kApBlock, smem);
-    per_sm = std::max(1, b);
-    smem_for = smem;
-  }
-  return per_sm;
+  return kernel_blocks_per_sm(reinterpret_cast<const void*>(k_allpairs), kApBlock, smem);
 }
 
 struct MatGraph {
@@ -133,8 +125,8 @@ struct MatGraph {
   }
 };
 
-std::mutex g_mu;
-std::map<std::vector<uint64_t>, std::shared_ptr<MatGraph>> g_graphs;
+// At most 16 argument sets keep a captured graph (graph_cache.cuh).
+GraphCache<std::vector<uint64_t>, MatGraph> g_graphs(16);
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -151,12 +143,7 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
     key.push_back(reinterpret_cast<uintptr_t>(d_as[i]));
     key.push_back(n_as[i]);
   }
-  std::shared_ptr<MatGraph> g;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_graphs.find(key);
-    if (it != g_graphs.end()) g = it->second;
-  }
+  std::shared_ptr<MatGraph> g = g_graphs.find(key);
   if (!g) {
     // Search method per database: the autotuner, timed on a sample of the
     // largest query set (at most 2^16 queries).
@@ -241,8 +228,7 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
     g->graph = graph;
     BITS_CUDA_TRY(cudaGraphInstantiate(&g->exec, graph, 0));
     g->kernels = 1;
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_graphs[key] = g;
+    g_graphs.put(key, g);
   }
   BITS_CUDA_TRY(cudaGraphLaunch(g->exec, st));
   count_launch((uint32_t)g->kernels);
@@ -250,13 +236,11 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
 }
 
 void release_matrix_graphs(const bits_db* db) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  for (auto it = g_graphs.begin(); it != g_graphs.end();) {
-    bool uses = false;
-    for (size_t k = 1; k < it->first.size(); ++k)
-      if (it->first[k] == reinterpret_cast<uintptr_t>(db)) uses = true;
-    it = uses ? g_graphs.erase(it) : std::next(it);
-  }
+  g_graphs.erase_if([db](const std::vector<uint64_t>& key) {
+    for (size_t k = 1; k < key.size(); ++k)
+      if (key[k] == reinterpret_cast<uintptr_t>(db)) return true;
+    return false;
+  });
 }
 
 }  // namespace bits

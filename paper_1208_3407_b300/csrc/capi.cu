@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "count.cuh"
@@ -64,6 +66,27 @@ int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap) {
   return b;
 }
 
+int kernel_blocks_per_sm(const void* kernel, int block, size_t smem, int cap) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, kernel, block, smem, cap);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int b = 0;
+  if (cap > 0) {
+    b = occupancy_with_l1(kernel, block, smem, cap);
+  } else {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, smem);
+    b = std::max(1, b);
+  }
+  cache.emplace(key, b);
+  return b;
+}
+
 bits_status pool_alloc(void** p, size_t bytes, cudaStream_t st) {
   static std::mutex mu;
   static std::vector<cudaMemPool_t> pools;
@@ -98,6 +121,10 @@ bits_status read_device_error(const bits_db* db, cudaStream_t st, bool clear) {
   BITS_CUDA_TRY(cudaMemcpyAsync(&h, db->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   BITS_CUDA_TRY(cudaStreamSynchronize(st));
   if (clear && h) BITS_CUDA_TRY(cudaMemsetAsync(db->err, 0, sizeof(uint32_t), st));
+  if (h & DEV_ERR_INTERNAL) {
+    set_error("a device-side consistency check failed (index out of range); results are invalid");
+    return BITS_EINTERNAL;
+  }
   if (h & DEV_ERR_TIMEOUT) {
     set_error("a bounded device-side wait timed out; results are invalid");
     return BITS_ETIMEOUT;

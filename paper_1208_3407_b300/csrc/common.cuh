@@ -15,6 +15,7 @@ namespace bits {
 enum : uint32_t {
   DEV_ERR_INVALID = 1u,   // an interval violated the input rules
   DEV_ERR_TIMEOUT = 2u,   // a bounded spin-wait gave up
+  DEV_ERR_INTERNAL = 4u,  // an internal consistency check failed (index out of range)
 };
 
 // Iterations a spin-wait may take (each sleeps ~100-200 ns) before it gives
@@ -33,6 +34,13 @@ int sm_count();
 // many CTAs need so the rest of the SM's on-chip memory stays L1 (defined in
 // capi.cu).
 int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap);
+// Resident CTAs per SM of `kernel` with `block` threads and `smem` bytes of
+// dynamic shared memory on the current device (at least 1), after raising
+// the kernel's dynamic shared-memory limit to `smem` on that device.  Both
+// are per-device settings, so the result is cached per (device, kernel,
+// block, smem) under a lock; with cap > 0 it goes through
+// occupancy_with_l1 (carveout fitted to `cap` CTAs).
+int kernel_blocks_per_sm(const void* kernel, int block, size_t smem, int cap = 0);
 bits_status cuda_status(cudaError_t e, const char* what);
 // Device memory from the library's stream-ordered pool, one per device,
 // created at first use: database blocks and every temporary (sort buffers,

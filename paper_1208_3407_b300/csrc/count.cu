@@ -1,6 +1,6 @@
 // bits_count kernels: Algorithm 2's counting loop over Algorithm 1 (ICount).
 //
-// One thread per query (Sec. 2.4 assigns one ICount per thread): a coalesced
+// One thread per query (Sec. "Parallel BITS" assigns one ICount per thread): a coalesced
 // 8-byte load of (start, end), the two top-level searches in shared memory,
 // the quad-cooperative descent through the 16-ary levels (search.cuh), a
 // coalesced 4-byte store of the count, and a block reduction of the 64-bit
@@ -106,16 +106,7 @@ __global__ void k_interleave_level0(const uint4* __restrict__ bs, const uint4* _
 }
 
 int count_blocks_per_sm(size_t smem) {
-  static int per_sm = 0;
-  static size_t smem_for = 0;
-  if (per_sm == 0 || smem_for != smem) {
-    cudaFuncSetAttribute(k_count_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_count_search, kCountBlock, smem);
-    per_sm = std::max(1, b);
-    smem_for = smem;
-  }
-  return per_sm;
+  return kernel_blocks_per_sm(reinterpret_cast<const void*>(k_count_search), kCountBlock, smem);
 }
 
 }  // namespace

@@ -7,6 +7,7 @@
 #include <tuple>
 
 #include "common.cuh"
+#include "graph_cache.cuh"
 #include "search.cuh"
 
 // One sorted array's learned index (a two-stage recursive model): a linear
@@ -59,12 +60,11 @@ struct bits_db {
   uint2* enum_e = nullptr;   // (end, index) in start order, for enumeration (device; optional)
   void* block = nullptr;     // the one device allocation owning all of the above
   size_t block_bytes = 0;
-  // Cached MC graphs keyed by the call's arguments.
-  std::mutex mu;
-  std::map<std::tuple<int, const void*, uint64_t, const void*, const void*, uint32_t, uint64_t,
-                      uint32_t, uint32_t, void*, void*>,
-           std::shared_ptr<bits_mc_graph>>
-      mc_graphs;
+  // Cached MC graphs keyed by the call's arguments (method, queries, n,
+  // contig table, seed, shuffle range, totals), at most 16.
+  using McKey = std::tuple<int, const void*, uint64_t, const void*, const void*, uint32_t, uint64_t,
+                           uint32_t, uint32_t, void*>;
+  bits::GraphCache<McKey, bits_mc_graph> mc_graphs{16};
 };
 
 namespace bits {

@@ -1,6 +1,7 @@
-// Enumeration problem (Sec. 1.1: report every intersecting pair) with the
-// count as the stopping rule of the scan (Sec. 2.2: |I(B, a)| terminates the
-// enumeration that a single binary search could not).
+// Enumeration problem (Sec. "Interval Set Intersection problem": report every
+// intersecting pair) with the count as the stopping rule of the scan (Sec. "BITS
+// Algorithm": |I(B, a)| terminates the enumeration that a single binary search could
+// not).
 //
 // Offsets: per-query counts (the count kernel) and an exclusive scan into
 // uint64 offsets, offsets[n] = number of pairs.  The scan is three plain
@@ -173,16 +174,7 @@ k_enumerate(const uint2* __restrict__ a, uint32_t n, LevelIndex L, uint32_t nb,
 }
 
 int enum_blocks_per_sm(size_t smem) {
-  static int per_sm = 0;
-  static size_t smem_for = 0;
-  if (per_sm == 0 || smem_for != smem) {
-    cudaFuncSetAttribute(k_enumerate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enumerate, kEnumBlock, smem);
-    per_sm = std::max(1, b);
-    smem_for = smem;
-  }
-  return per_sm;
+  return kernel_blocks_per_sm(reinterpret_cast<const void*>(k_enumerate), kEnumBlock, smem);
 }
 
 }  // namespace

@@ -1,4 +1,4 @@
-// Monte-Carlo significance test (Sec. 3.2): each shuffle re-places every
+// Monte-Carlo significance test (Sec. "Monte Carlo Simulations"): each shuffle re-places every
 // query interval uniformly inside its own contig (length kept) and recounts
 // it against the fixed database; the observed total is the count of the
 // unshuffled queries; k_ge = #{s : total_s >= observed}.
@@ -23,6 +23,7 @@
 #include "rmi.cuh"
 
 struct bits_mc_graph {
+  std::mutex run_mu;  // one replay at a time: d_scalars is read back after each
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   unsigned long long* d_scalars = nullptr;  // [0] observed, [1] k_ge
@@ -102,14 +103,8 @@ size_t mc_smem_bytes(const LevelIndex& L, uint32_t nc, bool rmi) {
 
 template <bool kRmi>
 int mc_blocks_per_sm(size_t smem) {
-  static int per_sm = 0;
-  static size_t smem_for = 0;
-  if (per_sm == 0 || smem_for != smem) {
-    per_sm = occupancy_with_l1(reinterpret_cast<const void*>(k_mc_search<kRmi>), kMcBlock, smem,
-                               kMcCtasPerSm);
-    smem_for = smem;
-  }
-  return per_sm;
+  return kernel_blocks_per_sm(reinterpret_cast<const void*>(k_mc_search<kRmi>), kMcBlock, smem,
+                              kMcCtasPerSm);
 }
 
 // Enqueue the whole test on `st` (used once, under stream capture).
@@ -177,15 +172,10 @@ bits_status run_mc(bits_db* db, int method, const uint32_t* d_a, uint32_t n,
     return BITS_EINVAL;
   }
   const uint32_t n_shuffles = shuffle_end - shuffle_begin;
-  auto key = std::make_tuple(method, (const void*)d_a, (uint64_t)n, (const void*)d_contig_off,
-                             (const void*)d_contig_len, n_contigs, seed, shuffle_begin,
-                             shuffle_end, (void*)d_totals, (void*)nullptr);
-  std::shared_ptr<bits_mc_graph> g;
-  {
-    std::lock_guard<std::mutex> lk(db->mu);
-    auto it = db->mc_graphs.find(key);
-    if (it != db->mc_graphs.end()) g = it->second;
-  }
+  const bits_db::McKey key(method, (const void*)d_a, (uint64_t)n, (const void*)d_contig_off,
+                           (const void*)d_contig_len, n_contigs, seed, shuffle_begin, shuffle_end,
+                           (void*)d_totals);
+  std::shared_ptr<bits_mc_graph> g = db->mc_graphs.find(key);
   if (!g) {
     g = std::make_shared<bits_mc_graph>();
     BITS_CUDA_TRY(cudaMalloc(&g->d_scalars, 2 * sizeof(unsigned long long)));
@@ -211,9 +201,11 @@ bits_status run_mc(bits_db* db, int method, const uint32_t* d_a, uint32_t n,
     BITS_CUDA_TRY(cudaGraphInstantiate(&g->exec, graph, 0));
     g->kernels_per_replay = bits_kernel_launches() - before;
     uncount_launch(g->kernels_per_replay);
-    std::lock_guard<std::mutex> lk(db->mu);
-    db->mc_graphs[key] = g;
+    db->mc_graphs.put(key, g);
   }
+  // Concurrent calls with the same arguments share the graph and its result
+  // words: replay, read back and check one call at a time.
+  std::lock_guard<std::mutex> run_lk(g->run_mu);
   BITS_CUDA_TRY(cudaGraphLaunch(g->exec, st));
   count_launch((uint32_t)g->kernels_per_replay);
   unsigned long long h[2] = {0, 0};
@@ -227,8 +219,7 @@ bits_status run_mc(bits_db* db, int method, const uint32_t* d_a, uint32_t n,
 }
 
 void release_mc_graphs(bits_db* db) {
-  std::lock_guard<std::mutex> lk(db->mu);
-  db->mc_graphs.clear();
+  db->mc_graphs.erase_if([](const bits_db::McKey&) { return true; });
 }
 
 }  // namespace bits

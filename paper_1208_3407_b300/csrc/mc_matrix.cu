@@ -1,4 +1,4 @@
-// Monte-Carlo screen over many query sets and databases (Sec. 3.3: every
+// Monte-Carlo screen over many query sets and databases (Sec. "Novel genomic relationships": every
 // pair of the 159 tracks, 1e4 shuffles each).  For query set i and database
 // j, totals[i][j][s] is the count of set i re-placed by shuffle s against
 // database j, the observed matrix is bits_count_matrix's, and the optional
@@ -120,14 +120,8 @@ k_mc_matrix(McMatArgs P) {
 }
 
 int mcm_blocks_per_sm(size_t smem) {
-  static int per_sm = 0;
-  static size_t smem_for = 0;
-  if (per_sm == 0 || smem_for != smem) {
-    per_sm = occupancy_with_l1(reinterpret_cast<const void*>(k_mc_matrix), kMcBlock, smem,
-                               kMcCtasPerSm);
-    smem_for = smem;
-  }
-  return per_sm;
+  return kernel_blocks_per_sm(reinterpret_cast<const void*>(k_mc_matrix), kMcBlock, smem,
+                              kMcCtasPerSm);
 }
 
 struct McMatGraph {
@@ -141,8 +135,8 @@ struct McMatGraph {
   }
 };
 
-std::mutex g_mu;
-std::map<std::vector<uint64_t>, std::shared_ptr<McMatGraph>> g_graphs;
+// At most 16 argument sets keep a captured graph (graph_cache.cuh).
+GraphCache<std::vector<uint64_t>, McMatGraph> g_graphs(16);
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -166,12 +160,7 @@ bits_status run_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint32
     key.push_back(reinterpret_cast<uintptr_t>(d_as[i]));
     key.push_back(n_as[i]);
   }
-  std::shared_ptr<McMatGraph> g;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_graphs.find(key);
-    if (it != g_graphs.end()) g = it->second;
-  }
+  std::shared_ptr<McMatGraph> g = g_graphs.find(key);
   if (!g && n_shuffles) {
     std::vector<McDb> hd(n_db);
     size_t max_top = 4;
@@ -255,8 +244,7 @@ bits_status run_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint32
     if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture(mc_matrix)");
     g->graph = graph;
     BITS_CUDA_TRY(cudaGraphInstantiate(&g->exec, graph, 0));
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_graphs[key] = g;
+    g_graphs.put(key, g);
   }
   if (g) {
     BITS_CUDA_TRY(cudaGraphLaunch(g->exec, st));
@@ -268,13 +256,11 @@ bits_status run_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint32
 }
 
 void release_mc_matrix_graphs(const bits_db* db) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  for (auto it = g_graphs.begin(); it != g_graphs.end();) {
-    bool uses = false;
-    for (size_t k = 7; k < it->first.size(); ++k)
-      if (it->first[k] == reinterpret_cast<uintptr_t>(db)) uses = true;
-    it = uses ? g_graphs.erase(it) : std::next(it);
-  }
+  g_graphs.erase_if([db](const std::vector<uint64_t>& key) {
+    for (size_t k = 7; k < key.size(); ++k)
+      if (key[k] == reinterpret_cast<uintptr_t>(db)) return true;
+    return false;
+  });
 }
 
 }  // namespace bits

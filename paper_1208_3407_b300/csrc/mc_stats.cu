@@ -1,8 +1,8 @@
-// Summary of Monte-Carlo tests (Sec. 3.2 tally, Sec. 3.3 / Fig. 3 score):
-// for each test, k_ge = #{T_s >= observed}, k_le = #{T_s <= observed}, the
-// two middle totals (ranks floor((N-1)/2) and floor(N/2) of the sorted
-// totals), the enrichment and depletion p-values and the score
-// log2(observed / median).
+// Summary of Monte-Carlo tests (Sec. "Monte Carlo Simulations" tally, Sec.
+// "Novel genomic relationships" / Fig. 3 score): for each test, k_ge = #{T_s
+// >= observed}, k_le = #{T_s <= observed}, the two middle totals (ranks
+// floor((N-1)/2) and floor(N/2) of the sorted totals), the enrichment and
+// depletion p-values and the score log2(observed / median).
 //
 // One CTA per test.  The middles come from a most-significant-digit radix
 // select over the 64-bit totals, both ranks in the same passes: a pass

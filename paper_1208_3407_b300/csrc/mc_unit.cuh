@@ -1,4 +1,4 @@
-// Device pieces of one Monte-Carlo work unit (Sec. 3.2), shared by the
+// Device pieces of one Monte-Carlo work unit (Sec. "Monte Carlo Simulations"), shared by the
 // single-test kernel (mc.cu) and the screen kernel over many query sets and
 // databases (mc_matrix.cu).
 //

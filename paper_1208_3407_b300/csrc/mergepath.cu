@@ -70,7 +70,7 @@ k_mp_merge(const uint32_t* __restrict__ X, uint32_t n, const uint32_t* __restric
   // Splits of a sorted pair of arrays always satisfy these; anything else
   // means unsorted input, reported instead of read.
   if (x1 < x0 || d1 - x1 < d0 - x0 || (uint64_t)(x1 - x0) + (d1 - x1) - (d0 - x0) > kMpTile) {
-    if (threadIdx.x == 0) set_dev_error(err, DEV_ERR_TIMEOUT);
+    if (threadIdx.x == 0) set_dev_error(err, DEV_ERR_INTERNAL);
     return;
   }
   const uint32_t nx = x1 - x0, ny = y1 - y0;

@@ -100,6 +100,11 @@ extern "C" bits_status bits_sort_intervals_noalloc(const uint32_t* d_b, uint64_t
   uint32_t h = 0;
   BITS_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   BITS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h & DEV_ERR_INTERNAL) {
+    set_error("bits_sort_intervals_noalloc: a device-side consistency check failed (sort "
+              "scatter index out of range)");
+    return BITS_EINTERNAL;
+  }
   if (h & DEV_ERR_TIMEOUT) {
     set_error("bits_sort_intervals_noalloc: a bounded device-side wait timed out");
     return BITS_ETIMEOUT;

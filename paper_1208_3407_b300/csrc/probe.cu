@@ -1,5 +1,6 @@
 // bits_probe_random_reads: the rate at which this GPU serves random 64-byte
-// node reads from DRAM.
+// node reads from DRAM.  Built into its own library, libbits_probe.so (a
+// measurement aid for the benchmark, not part of the method).
 //
 // Every search kernel here reads one 64-byte node per level of the 16-ary
 // tree, loaded by a quad of lanes (16 bytes each) with a 64-byte line fill.
@@ -15,6 +16,7 @@
 // of one random 128-byte line, as a query does whose two searches (starts
 // and ends) meet in one interleaved node pair.
 #include "common.cuh"
+#include "../../include/bits_probe.h"
 
 namespace bits {
 namespace {

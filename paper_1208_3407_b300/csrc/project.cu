@@ -1,5 +1,5 @@
-// Projection onto one coordinate line (Sec. 2.3) and closed-to-half-open
-// conversion (Sec. 1.1 states its predicate for closed intervals).
+// Projection onto one coordinate line (Sec. "BITS Algorithm" (projection)) and closed-to-half-open
+// conversion (Sec. "Interval Set Intersection problem" states its predicate for closed intervals).
 //
 // Interval i on chromosome c = chrom[i] becomes [off[c] + start, off[c] + end)
 // (end + 1 for closed input, since [s, e] on the integers is [s, e + 1)).

@@ -1,5 +1,6 @@
 // Projection of chromosome-local (optionally closed) intervals onto the
-// half-open genome-wide line every other kernel works on (Sec. 2.3, Sec. 1.1).
+// half-open genome-wide line every other kernel works on (Sec. "BITS
+// Algorithm" (projection), Sec. "Interval Set Intersection problem").
 #pragma once
 
 #include "common.cuh"

@@ -1,5 +1,5 @@
 // LSD radix sort of interval starts and ends (Algorithm 2's two Sort steps;
-// Sec. 2.4 relies on a GPU radix sort for them), keys only or key/value.
+// Sec. "Parallel BITS" relies on a GPU radix sort for them), keys only or key/value.
 //
 // Design (one GPU, HBM-bound):
 //   * k_radix_hist reads the interval array once, validates it, and builds
@@ -315,7 +315,7 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
       oob = true;
     }
   }
-  if (oob) set_dev_error(err, DEV_ERR_TIMEOUT);
+  if (oob) set_dev_error(err, DEV_ERR_INTERNAL);
 }
 
 size_t sweep_smem(bool kv) {
@@ -323,14 +323,11 @@ size_t sweep_smem(bool kv) {
          ((kv ? 2 : 1) * kSwTile + kSwWarps * kCnt + 5 * kRadix + kRadix / 32 + 4);
 }
 
+// Raises k_onesweep's dynamic shared-memory limit on the current device
+// (once per device, through the per-device cache).
 template <bool KV>
 void prepare_sweep() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(k_onesweep<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sweep_smem(KV));
-    done = true;
-  }
+  kernel_blocks_per_sm(reinterpret_cast<const void*>(k_onesweep<KV>), kSwBlock, sweep_smem(KV));
 }
 
 }  // namespace
@@ -360,7 +357,7 @@ bits_status radix_sort_pairs(const uint2* d_src, uint32_t n, const SortSpec spec
   BITS_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   BITS_CUDA_TRY(cudaStreamSynchronize(st));
   if (!validate && (h_err & DEV_ERR_INVALID)) {
-    set_error("bits_build_db: a database interval has end <= start");
+    set_error("a database interval has end <= start");
     return BITS_EINVAL;
   }
   if (any_inverted) *any_inverted = h_hist[2 * kPasses * kRadix] != 0;

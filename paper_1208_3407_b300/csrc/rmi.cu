@@ -199,13 +199,7 @@ k_count_rmi(const uint2* __restrict__ a, uint32_t n, LevelIndex L, RmiView R, ui
 }
 
 int rmi_count_blocks_per_sm() {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_count_rmi, kCountBlock, 0);
-    per_sm = std::max(1, b);
-  }
-  return per_sm;
+  return kernel_blocks_per_sm(reinterpret_cast<const void*>(k_count_rmi), kCountBlock, 0);
 }
 
 }  // namespace

@@ -3,7 +3,7 @@
 // sorted uint32 array X -- Algorithm 1's BSearch expressed as a count:
 //     first = #(B_S < a.end)
 //     last  = #(B_E <= a.start) = #(B_E < a.start + 1)   (a.start < 2^32 - 1)
-// so ICount(a) = first - last (Sec. 2.2).  Only one primitive, "count of
+// so ICount(a) = first - last (Sec. "BITS Algorithm").  Only one primitive, "count of
 // elements below key", is needed.
 //
 // Implicit 16-ary search tree over each sorted array (built by

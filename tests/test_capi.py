@@ -54,17 +54,6 @@ def test_host_side_argument_checks(lib):
                              C.byref(h)) == _lib.BITS_EINVAL
     assert lib.bits_count(None, None, 0, None, None, None) == _lib.BITS_EINVAL
     assert lib.bits_count_host(None, 1, None, 0, None, None, None) == _lib.BITS_EINVAL
-    rate = C.c_double()
-    assert lib.bits_probe_random_reads(None, 1 << 20, 1, 1, C.byref(rate),
-                                       None) == _lib.BITS_EINVAL
-    assert lib.bits_probe_random_reads(C.c_void_p(256), 100, 1, 1, C.byref(rate),
-                                       None) == _lib.BITS_EINVAL
-    assert lib.bits_probe_random_reads(C.c_void_p(256), 1 << 20, 0, 1, C.byref(rate),
-                                       None) == _lib.BITS_EINVAL
-    assert lib.bits_probe_random_reads(C.c_void_p(256), 1 << 20, 1, 3, C.byref(rate),
-                                       None) == _lib.BITS_EINVAL
-    assert lib.bits_probe_random_reads(C.c_void_p(64), 1 << 20, 1, 2, C.byref(rate),
-                                       None) == _lib.BITS_EINVAL
     assert lib.bits_check(None, None) == _lib.BITS_EINVAL
     assert lib.bits_db_info(None, None, None, None, None) == _lib.BITS_EINVAL
     assert lib.bits_mc(None, 0, None, 0, None, None, 0, 0, 0, 0, None, None, None, None,
@@ -99,6 +88,28 @@ def test_host_side_argument_checks(lib):
     assert lib.bits_enumerate_pairs(None, None, 0, None, None, None) == _lib.BITS_EINVAL
     lib.bits_free(None)
     assert lib.bits_kernel_launches() == 0
+
+
+def test_probe_library_exports_and_checks(lib):
+    """The measurement probe lives in libbits_probe.so (include/bits_probe.h),
+    outside the library's own C ABI; its argument checks return codes."""
+    from paper_1208_3407_b300 import _lib, probe
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "bits_probe.h")).read(),
+                  flags=re.S)
+    declared = sorted(set(re.findall(r"\b(bits_[a-z_0-9]+)\s*\(", text)))
+    assert declared == sorted(probe.EXPORTS)
+    plib = probe.load()
+    for name in declared:
+        assert hasattr(plib, name), name
+        assert not hasattr(lib, name), name            # not in the method's library
+    rate = C.c_double()
+    f = plib.bits_probe_random_reads
+    assert f(None, 1 << 20, 1, 1, C.byref(rate), None) == _lib.BITS_EINVAL
+    assert f(C.c_void_p(256), 100, 1, 1, C.byref(rate), None) == _lib.BITS_EINVAL
+    assert f(C.c_void_p(256), 1 << 20, 0, 1, C.byref(rate), None) == _lib.BITS_EINVAL
+    assert f(C.c_void_p(256), 1 << 20, 1, 3, C.byref(rate), None) == _lib.BITS_EINVAL
+    assert f(C.c_void_p(64), 1 << 20, 1, 2, C.byref(rate), None) == _lib.BITS_EINVAL
+    assert b"bits_probe_random_reads" in lib.bits_last_error()
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

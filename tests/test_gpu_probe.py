@@ -12,8 +12,8 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def bits():
-    import paper_1208_3407_b300 as bits
-    return bits
+    from paper_1208_3407_b300 import probe
+    return probe
 
 
 def test_dram_rate_is_plausible_and_below_l2_rate(bits):
@@ -31,9 +31,8 @@ def test_dram_rate_is_plausible_and_below_l2_rate(bits):
 
 
 def test_argument_errors(bits):
-    from paper_1208_3407_b300 import _lib
     import ctypes as C
-    lib = _lib.load()
+    lib = bits.load()
     buf = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     rate = C.c_double()
     assert lib.bits_probe_random_reads(buf.data_ptr(), 1000, 16, 1, C.byref(rate), None) == 1
