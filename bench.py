@@ -1,26 +1,41 @@
 """Benchmark of the BITS hot path on B300 (one JSON line on stdout).
 
-Headline workload (one "step"): bits_count of the exome-vs-reads shape --
-200,000 query intervals (lengths N(150, 30)) against a resident database of
-20,000,000 reads (length 100, 70 % from 200,000 Gaussian hotspots) on a
-24-contig genome -- Algorithm 2's counting loop over Algorithm 1, per-query
-uint32 counts plus the uint64 total.  L2 is flushed before every timed step.
+Headline workload (one "step"): bits_count of the learned-index workload at
+scale -- 100,000,000 query intervals placed uniformly on a 3.0 Gbp line
+against a resident database of 100,000,000 intervals (80 % from a mixture of
+1000 Gaussians, 20 % uniform; lengths log-uniform in [50, 10^4]) with a
+learned index of 2^16 linear leaves per sorted array -- Algorithm 2's
+counting loop over Algorithm 1, per-query uint32 counts plus the uint64
+total.  The headline is the faster of the plain 16-ary search and the
+learned index; both are timed and reported side by side (with merge path).
+L2 is flushed before every timed step.
 
-Also reported on the same line: the database build (radix sort of B_S and
-B_E) and the one-shot form (build + count per step), the learned-index and
-merge-path forms of the same count, the count end to end through the C ABI
-with host buffers (bits_count_host), the projection and the enumeration of
-the same workload, the Monte-Carlo test (100,000 intervals vs 1,000,000,
-10,000 shuffles per launch), the 100M x 100M count in every form, the 64 x
-32 all-pairs count and Monte-Carlo screen, the random-read rates these
-kernels are set against (bits_probe_random_reads, DRAM and L2), and the CPU
-oracle timed on this host's cores.
+Also reported on the same line (most important last, so that a reader of
+the line's tail sees them): the random-read rates the search kernels are
+set against, the exome-vs-reads workload (200,000 queries vs 20,000,000
+reads: count forms, host-buffer count, build, one-shot build+count,
+projection, enumeration), the 64 x 32 all-pairs count and Monte-Carlo
+screen, the 100M database build, the headline's forms, and the Monte-Carlo
+significance test (100,000 intervals vs 1,000,000, 10,000 shuffles per
+launch: shuffles/s, placements/s, its L2 and issue rooflines).  Parity is
+checked in the run: every headline count of a 1M-query sample and the
+sorted arrays against the CPU oracle, all 10,000 Monte-Carlo totals and all
+2,048 all-pairs totals against the oracle's stored values.
+
+The CPU oracle is timed on this host (rank 0) by the protocol both arms
+share: count of a 1,000,000-query sample of the headline against the
+oracle-sorted database with all cores, of a 200,000-query sample
+single-threaded, and the oracle's database sort (std::sort) of 10,000,000
+of its intervals, each as mean and sd over 5 runs.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--detail PATH]
 
-Under torchrun each rank runs the same per-GPU workload (queries are
-independent, so the work shards with no collective); value is the sum over
-ranks divided by the slowest rank's time.
+Under torchrun (N > 1) the headline's queries and the Monte-Carlo test's
+shuffles are split across the ranks (each rank keeps its own copy of the
+database; no collective inside the timed region), so the job's total work
+is fixed and "scaling" is "strong"; value is all ranks' queries divided by
+the slowest rank's time.  The other workloads run on rank 0 only.
 """
 from __future__ import annotations
 
@@ -39,11 +54,35 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
 
 METRIC = "queries/s and MC shuffles/s on 1 B300, learned-index vs binary-search, bit-exact"
-HEADLINE = ("exome-vs-reads shape: 200,000 queries (len N(150,30) clipped [50,400], uniform) "
-            "vs 20,000,000 reads (len 100, 70% in 200,000 hotspots sigma 200 bp) on a "
-            "24-contig genome (seed 3)")
+HEADLINE = ("learned-index BITS at scale: 100,000,000 uniform queries vs 100,000,000 intervals "
+            "(80% from 1000 Gaussians sigma U[1e3,1e6], 20% uniform) on a 3.0 Gbp line, lengths "
+            "log-uniform [50,1e4], 2^16 linear leaves per sorted array")
+SAMPLE_ALL, SAMPLE_ONE, SAMPLE_BUILD, PROTOCOL_RUNS = 1_000_000, 200_000, 10_000_000, 5
+
+
+def config_dict(world: int) -> dict:
+    """The headline's config, identical in both arms."""
+    return {"workload": HEADLINE,
+            "method": "faster of plain 16-ary search and learned index (both in forms)",
+            "l2": "flushed (256 MB write) before every timed step; queries 800 MB > L2",
+            "parallelism": f"dp{world}: queries and shuffles split across ranks, database "
+                           "replicated, no collective in the timed region"}
+
+
+def sig(x, digits: int = 4):
+    """Round for the compact JSON line."""
+    if x is None or isinstance(x, (bool, str)):
+        return x
+    if isinstance(x, dict):
+        return {k: sig(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig(v, digits) for v in x]
+    if isinstance(x, int):
+        return x
+    return float(f"{x:.{digits}g}")
 
 
 # ---------------------------------------------------------------------------- helpers
@@ -93,21 +132,13 @@ def profiled_value(profile: str, field: str, sources):
     return float(t.group(1))
 
 
-def profiled_traffic(kernel: str, sources):
-    """DRAM bytes per launch recorded in profiles/ for this exact kernel source."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
-    if not os.path.exists(path):
-        return None
-    text = open(path).read()
-    m = re.search(r"source_digest:\s*([0-9a-f]+)", text)
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != source_digest(sources):
-        return None
-    return float(t.group(1))
+def mean_sd(xs):
+    return {"mean": statistics.fmean(xs), "sd": statistics.stdev(xs) if len(xs) > 1 else 0.0,
+            "runs": len(xs)}
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms (read only)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -134,9 +165,6 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append((time.time(), line.strip()))
-
-    def mark(self):
-        return time.time()
 
     def stop(self):
         if self.proc:
@@ -169,6 +197,39 @@ class ClockSampler:
                 "samples": len(loaded), "samples_in_timed_region": len(inside)}
 
 
+# ------------------------------------------------------------- the oracle protocol
+
+def oracle_protocol(o, a4, b4, bs4, be4, cores: int) -> dict:
+    """Both arms time the CPU oracle this way: count of a 1M-query sample of
+    the headline against the oracle-sorted 100M database with all cores and
+    of a 200k sample single-threaded, and the oracle's sort of 10M of the
+    database's intervals (single-threaded std::sort of both words), each 5
+    runs, as rates with mean and sd."""
+    def rate(fn, units):
+        xs = []
+        for _ in range(PROTOCOL_RUNS):
+            t = time.perf_counter()
+            fn()
+            xs.append(units / (time.perf_counter() - t))
+        return mean_sd(xs)
+    s_all, s_one, b_sub = a4[:SAMPLE_ALL], a4[:SAMPLE_ONE], b4[:SAMPLE_BUILD]
+    return {
+        "count_all_cores": rate(lambda: o.count_sorted(s_all, bs4, be4, threads=cores), SAMPLE_ALL),
+        "count_one_thread": rate(lambda: o.count_sorted(s_one, bs4, be4, threads=1), SAMPLE_ONE),
+        "build_one_thread": rate(lambda: o.build(b_sub), SAMPLE_BUILD),
+        "units": "queries/s (count), intervals/s (build)",
+        "cores": cores}
+
+
+def cpu_baseline_from(proto: dict) -> dict:
+    c = proto["count_all_cores"]
+    return {"value": c["mean"], "unit": "queries/s", "cores": proto["cores"], "kind": "oracle",
+            "sample": f"first {SAMPLE_ALL:,} headline queries against the full oracle-sorted "
+                      f"database, std::thread over all cores, mean of {c['runs']} runs "
+                      f"(sd {c['sd']:.3g}); single thread {proto['count_one_thread']['mean']:.3g} "
+                      f"q/s; oracle sort {proto['build_one_thread']['mean']:.3g} intervals/s"}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -179,29 +240,38 @@ def run_reference(args):
     import bits_synth
     import oracle
     o = oracle.get()
-    _, a, b = bits_synth.config2()
-    bs, be = o.build(b)
+    a4, b4 = bits_synth.config4()
+    bs4, be4 = o.build(b4)
     cores = os.cpu_count() or 1
-    sample = a[:20_000]
-    for _ in range(args.warmup):
-        o.count_sorted(sample, bs, be, threads=cores, want_counts=True)
+    n_samples = a4.shape[0] // SAMPLE_ALL
+
+    def step(i):
+        k = i % n_samples
+        o.count_sorted(a4[k * SAMPLE_ALL:(k + 1) * SAMPLE_ALL], bs4, be4, threads=cores)
+
+    for i in range(args.warmup):
+        step(i)
     times = []
-    for _ in range(args.steps):
+    for i in range(args.steps):
         t = time.perf_counter()
-        o.count_sorted(sample, bs, be, threads=cores, want_counts=True)
+        step(args.warmup + i)
         times.append(time.perf_counter() - t)
-    per_step = sum(times) / len(times)
-    qps = sample.shape[0] / per_step
+    per_step = statistics.fmean(times)
+    qps = SAMPLE_ALL / per_step
+    proto = oracle_protocol(o, a4, b4, bs4, be4, cores)
+    cpu = cpu_baseline_from(proto)
+    cpu["value"] = qps
+    cpu["sample"] = (f"{SAMPLE_ALL:,} headline queries per step (a different slice each step) "
+                     "against the full oracle-sorted database, all cores")
     line = {
         "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": HEADLINE, "sample": "first 20,000 of the 200,000 queries per step"},
-        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                         "sample": "first 20,000 queries per step against the full sorted B"},
+        "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": config_dict(world), "cpu_baseline": cpu,
         "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+        "protocol": sig(proto),
     }
     print(json.dumps(line))
 
@@ -212,8 +282,10 @@ def run_ours(args):
     import torch
 
     import bits_synth
+    import goldens
     import oracle
     import paper_1208_3407_b300 as bits
+    from paper_1208_3407_b300 import probe, sharding
 
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
@@ -221,9 +293,11 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    lead = rank == 0
     dev = torch.device("cuda", local)
     hbm_peak, peak_kind = peaks()
     o = oracle.get()
+    cores = os.cpu_count() or 1
 
     def barrier():
         if dist is not None:
@@ -242,12 +316,14 @@ def run_ours(args):
     def to_dev(x):
         return torch.from_numpy(np.ascontiguousarray(x, dtype=np.uint32)).to(dev)
 
-    def timed(fn, steps, warmup):
-        """Mean device ms of fn over `steps` runs, L2 flushed before each."""
+    def timed(fn, steps, warmup, all_ranks=True):
+        """Mean device ms of fn over `steps` runs (L2 flushed before each),
+        the kernels it launched per step, and the host time window."""
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
-        barrier()
+        if all_ranks:
+            barrier()
         torch.cuda.synchronize()
         l0 = bits.kernel_launches()
         ms = 0.0
@@ -262,367 +338,176 @@ def run_ours(args):
             ms += e0.elapsed_time(e1)
         torch.cuda.synchronize()
         t1 = time.time()
-        barrier()
-        return max_over_ranks(ms / steps), (bits.kernel_launches() - l0) / steps, (t0, t1)
+        if all_ranks:
+            barrier()
+            return max_over_ranks(ms / steps), (bits.kernel_launches() - l0) / steps, (t0, t1)
+        return ms / steps, (bits.kernel_launches() - l0) / steps, (t0, t1)
 
-    # The rate of random 64-byte node reads from DRAM (4 GiB buffer, best of
-    # three): the hardware bound of the search kernels on a database larger
-    # than L2, measured here beside them.
-    rand_peak = max(bits.probe_random_reads(4 << 30, 1 << 25, device=dev) for _ in range(3))
-    # The same access on a 32 MiB buffer, which L2 holds: the bound of the
-    # Monte-Carlo kernels, whose databases stay in L2.
-    l2_peak = max(bits.probe_random_reads(32 << 20, 1 << 25, device=dev) for _ in range(3))
+    # Random 64-byte node reads: from DRAM (4 GiB buffer) -- the bound of the
+    # searches on databases larger than L2 -- and from L2 (32 MiB buffer), the
+    # bound of the Monte-Carlo kernels; best of three each.
+    rand_peak = max(probe.probe_random_reads(4 << 30, 1 << 25, device=dev) for _ in range(3))
+    l2_peak = max(probe.probe_random_reads(32 << 20, 1 << 25, device=dev) for _ in range(3))
     torch.cuda.empty_cache()
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
     sampler = ClockSampler(int(vis) if vis.isdigit() else local)
     sampler.start()
+    detail = {}
 
-    # ---- headline: exome-vs-reads shape, database resident -------------------
-    genome, a_np, b_np = bits_synth.config2()
-    n_a, n_b = a_np.shape[0], b_np.shape[0]
-    a = to_dev(a_np)
-    b = to_dev(b_np)
-
-    # Algorithm 2's set-up (split + radix sort + search levels), plain database;
-    # each database is freed after its timed region.
-    build_list = []
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        l0 = bits.kernel_launches()
+    # ================= headline: 100M queries vs 100M intervals ================
+    a4_np, b4_np = bits_synth.config4()
+    n4 = a4_np.shape[0]
+    lo4, hi4 = sharding.shard_bounds(n4, rank, world)
+    b4 = to_dev(b4_np)
+    build4 = []
+    for i in range(4):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
         e0.record(stream)
-        db_tmp = bits.Database(b)
+        d = bits.Database(b4, rmi_leaves_log2=16 if i % 2 else 0)
         e1.record(stream)
         e1.synchronize()
-        if i >= args.warmup:
-            build_list.append((e0.elapsed_time(e1), bits.kernel_launches() - l0))
-        db_tmp.free()
-    build_ms = max_over_ranks(sum(x for x, _ in build_list) / len(build_list))
-    build_launches = build_list[-1][1]
-
-    # One-shot form of the same workload (the paper's single intersection,
-    # Fig. 2: setup + count): build the database from the 20M reads, count
-    # the 200k queries, free it -- per step.
-    one_counts = torch.empty(n_a, dtype=torch.uint32, device=dev)
-    one_total = torch.empty(1, dtype=torch.uint64, device=dev)
-
-    def one_shot_step():
-        d = bits.Database(b)
-        d.count(a, counts=one_counts, total=one_total, method=bits.METHOD_SEARCH, check=False)
-        d.free()
-
-    one_ms, one_launches, _ = timed(one_shot_step, args.steps, args.warmup)
-    t_rmi = time.time()
-    db = bits.Database(b, rmi_leaves_log2=16)          # plain levels + learned index
-    torch.cuda.synchronize()
-    build_rmi_s = time.time() - t_rmi
-
-    counts = torch.empty(n_a, dtype=torch.uint32, device=dev)
-    total = torch.empty(1, dtype=torch.uint64, device=dev)
-
-    def count_with(method):
-        return lambda: db.count(a, counts=counts, total=total, method=method, check=False)
-
+        build4.append((i % 2, e0.elapsed_time(e1)))
+        if i < 3:
+            d.free()
+    db4 = d                                             # plain levels + learned index
+    del b4
+    a4 = to_dev(a4_np[lo4:hi4])
+    n_mine = hi4 - lo4
+    c4 = torch.empty(n_mine, dtype=torch.uint32, device=dev)
+    t4 = torch.empty(1, dtype=torch.uint64, device=dev)
     forms = {}
-    for name, m in (("search", bits.METHOD_SEARCH), ("rmi", bits.METHOD_RMI)):
-        ms, _, _ = timed(count_with(m), args.steps, args.warmup)
-        forms[name] = {"ms_per_step": ms, "queries_per_s": world * n_a / (ms * 1e-3)}
-        db.check()
-    # AUTO (bits_count's default): its autotuner times back to back (warm L2)
-    db.count(a, counts=counts, total=total, check=True)          # tunes this size class
-    auto_ms, _, _ = timed(count_with(None), args.steps, args.warmup)
-    forms["auto"] = {"ms_per_step": auto_ms, "queries_per_s": world * n_a / (auto_ms * 1e-3)}
-    # headline: the faster form under the cold-L2 protocol, timed again
-    head = min(("search", "rmi"), key=lambda k: forms[k]["ms_per_step"])
+    totals4 = {}
+    for name, m, per_query in (("search", bits.METHOD_SEARCH, True),
+                               ("rmi", bits.METHOD_RMI, True),
+                               ("mergepath", bits.METHOD_MERGEPATH, True),
+                               ("search_total_only", bits.METHOD_SEARCH, False)):
+        out_c = c4 if per_query else False
+        ms, launches, _ = timed(lambda m=m, out_c=out_c: db4.count(a4, counts=out_c, total=t4,
+                                                                   method=m, check=False),
+                                args.steps, args.warmup)
+        totals4[name] = int(t4.cpu().numpy()[0])
+        forms[name] = {"ms": ms, "queries_per_s": n4 / (ms * 1e-3), "gpu_launches": launches}
+    db4.check()
+    assert len(set(totals4.values())) == 1, totals4
+    db4.count(a4, counts=c4, total=t4, check=True)           # AUTO: tunes this size class
+    auto_ms, _, _ = timed(lambda: db4.count(a4, counts=c4, total=t4, check=False), args.steps,
+                          args.warmup)
+    forms["auto"] = {"ms": auto_ms, "queries_per_s": n4 / (auto_ms * 1e-3)}
+    head = min(("search", "rmi"), key=lambda k: forms[k]["ms"])
     head_m = bits.METHOD_SEARCH if head == "search" else bits.METHOD_RMI
-    head_ms, launches, window = timed(count_with(head_m), args.steps, args.warmup)
-    db.check()
+    head_ms, launches, window = timed(lambda: db4.count(a4, counts=c4, total=t4, method=head_m,
+                                                        check=False), args.steps, args.warmup)
+    db4.check()
     clocks = sampler.summary(*window)
-    auto_method = head
-    got = counts.cpu().numpy()
-    idx = np.random.default_rng(0).choice(n_a, size=256, replace=False)
-    oc, _ = o.count_brute(a_np[idx], b_np)
-    parity_ok = bool(np.array_equal(got[idx], oc))
+    combined = sharding.combine_totals(int(t4.cpu().numpy()[0])) if dist else \
+        int(t4.cpu().numpy()[0])
+
+    # Parity of the headline against the oracle: the sorted arrays, and every
+    # count of the first 1M queries (the oracle sorts the database itself).
+    parity = {}
+    bs4 = be4 = None
+    if lead:
+        bs4, be4 = o.build(b4_np)
+        gs, ge = db4.sorted_arrays()
+        parity["headline_sorted_arrays"] = bool(np.array_equal(gs.cpu().numpy(), bs4) and
+                                                np.array_equal(ge.cpu().numpy(), be4))
+        k = min(SAMPLE_ALL, n_mine)
+        oc, _ = o.count_sorted(a4_np[lo4:lo4 + k], bs4, be4, threads=cores)
+        parity["headline_counts_1m_sample"] = bool(np.array_equal(c4[:k].cpu().numpy(), oc))
+    if dist is not None and lead:
+        full = torch.empty(1, dtype=torch.uint64, device=dev)
+        db4.count(to_dev(a4_np), counts=False, total=full, method=bits.METHOD_SEARCH)
+        parity["sharded_total_equals_single_gpu"] = int(full.cpu().numpy()[0]) == combined
 
     # End to end through the C ABI with host buffers: bits_count_host reads the
-    # page-locked queries and writes the counts in place over the bus, copies
-    # the total back and synchronises -- every byte crosses inside the timed
-    # region.  Beside it, the staged form: torch copies around the
-    # device-resident call.
-    a_host = torch.from_numpy(a_np.astype(np.uint32)).pin_memory()
-    counts_host = torch.zeros(n_a, dtype=torch.uint32).pin_memory()
-    total_host_p = torch.zeros(1, dtype=torch.uint64).pin_memory()
+    # page-locked queries and writes the page-locked counts in place over the
+    # bus and copies the total back -- every byte crosses inside the timed step.
+    a_host = torch.from_numpy(np.ascontiguousarray(a4_np[lo4:hi4])).pin_memory()
+    counts_host = torch.zeros(n_mine, dtype=torch.uint32).pin_memory()
+    total_host = torch.zeros(1, dtype=torch.uint64).pin_memory()
 
     def e2e_step():
-        db.count_host(a_host, counts=counts_host, total=total_host_p, method=head_m,
-                      check=False)
+        db4.count_host(a_host, counts=counts_host, total=total_host, method=head_m, check=False)
 
     e2e_ms, e2e_launches, _ = timed(e2e_step, args.steps, args.warmup)
-    db.check()
-    e2e_ok = bool(np.array_equal(counts_host.numpy(), got) and
-                  int(total_host_p.numpy()[0]) == int(total.cpu().numpy()[0]))
-    counts_host_s = torch.empty(n_a, dtype=torch.uint32).pin_memory()
-    total_host = torch.empty(1, dtype=torch.uint64).pin_memory()
-    a_stage = torch.empty_like(a)
+    db4.check()
+    parity["headline_host_buffers"] = bool(
+        np.array_equal(counts_host.numpy(), c4.cpu().numpy()) and
+        int(total_host.numpy()[0]) == int(t4.cpu().numpy()[0]))
+    del a_host, counts_host
 
-    def e2e_staged_step():
-        a_stage.copy_(a_host, non_blocking=True)
-        db.count(a_stage, counts=counts, total=total, method=head_m, check=False)
-        counts_host_s.copy_(counts, non_blocking=True)
-        total_host.copy_(total, non_blocking=True)
+    rmi_src = ["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/rmi_search.cuh",
+               "paper_1208_3407_b300/csrc/rmi.cu"]
+    search_src = ["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/count.cu"]
+    kernel = "k_count_rmi" if head == "rmi" else "k_count_search"
+    src = rmi_src if head == "rmi" else search_src
+    # DRAM bytes per query from the ncu capture named in profiles/ (valid
+    # while the kernel's sources are unchanged), times this rank's queries.
+    traffic_q = profiled_value(f"{kernel}_100m", "dram_bytes_per_query", src)
+    achieved = 76.0 * n4 / (head_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak,
+                "traffic": traffic_q * n_mine if traffic_q else None,
+                "peak_source": peak_kind, "kernel": kernel,
+                "algorithmic_bytes_per_query": 76}
+    random_access = {"bound": "random 64-B node reads from DRAM (probe, 4 GiB)",
+                     "achieved": 2.0 * n4 / (head_ms * 1e-3), "peak": rand_peak,
+                     "unit": "nodes/s", "frac": 2.0 * n4 / (head_ms * 1e-3) / rand_peak,
+                     "nodes_per_query": 2}
+    db4.free()
+    del a4, c4
 
-    e2e_staged_ms, _, _ = timed(e2e_staged_step, args.steps, args.warmup)
-    db.free()
-
-    # ---- projection (Sec. 2.3) of 20M chromosome-local closed reads ------------
-    # A pure stream: 12 B read (chromosome id, start, end) + 8 B written per
-    # interval, so its roofline is HBM bandwidth.
-    pc_np, ps_np, pe_np = bits_synth.local_intervals(genome, n_b, seed=5, lo=100, hi=100,
-                                                     closed=True)
-    pc, ps, pe = to_dev(pc_np), to_dev(ps_np), to_dev(pe_np)
-    pco, pcl = to_dev(genome.offsets), to_dev(genome.lengths)
-    p_out = torch.empty((n_b, 2), dtype=torch.uint32, device=dev)
-
-    def project_step():
-        bits.project(ps, pe, contig=pc, contig_off=pco, contig_len=pcl, closed=True, out=p_out)
-
-    proj_ms, proj_launches, _ = timed(project_step, args.steps, args.warmup)
-    idx = np.random.default_rng(1).choice(n_b, size=4096, replace=False)
-    exp_p, _ = o.project(pc_np[idx], ps_np[idx], pe_np[idx], genome.offsets, genome.lengths,
-                         closed=True)
-    proj_ach = 20.0 * n_b / (proj_ms * 1e-3) / 1e9
-    project = {"ms": proj_ms, "intervals": n_b, "intervals_per_s": world * n_b / (proj_ms * 1e-3),
-               "gpu_launches": proj_launches,
-               "parity_sample_ok": bool(np.array_equal(p_out.cpu().numpy()[idx], exp_p)),
-               "roofline": {"bound": "hbm", "achieved": proj_ach, "peak": hbm_peak, "unit": "GB/s",
-                            "frac": proj_ach / hbm_peak, "peak_source": peak_kind,
-                            "kernel": "k_project<true>", "algorithmic_bytes_per_interval": 20}}
-    del pc, ps, pe, p_out
-
-    # ---- enumeration (Sec. 1.1): every pair of the exome-vs-reads workload ----
-    db_en = bits.Database(b, enumerate=True)
-
-    def enum_step():
-        db_en.enumerate(a, check=False)
-
-    en_ms, en_launches, _ = timed(enum_step, args.steps, args.warmup)
-    db_en.check()
-    off_g, pairs_g = db_en.enumerate(a)
-    idx = np.random.default_rng(2).choice(n_a, size=64, replace=False)
-    eoff, epairs = o.enumerate_scan(a_np[idx], b_np)
-    off_np, pairs_np = off_g.cpu().numpy(), pairs_g.cpu().numpy()
-    en_ok = True
-    for k, i in enumerate(idx):
-        got = pairs_np[int(off_np[i]):int(off_np[i + 1]), 1]
-        en_ok &= bool(np.array_equal(got, epairs[int(eoff[k]):int(eoff[k + 1]), 1]))
-    n_pairs = int(off_np[-1])
-    enumerate_ = {"ms": en_ms, "queries": n_a, "pairs": n_pairs,
-                  "queries_per_s": world * n_a / (en_ms * 1e-3),
-                  "pairs_per_s": world * n_pairs / (en_ms * 1e-3), "gpu_launches": en_launches,
-                  "parity_sample_ok": en_ok,
-                  "note": "offsets pass (count + scan), one read of the pair count, pairs pass"}
-    db_en.free()
-    del off_g, pairs_g
-
-    # ---- Monte-Carlo test (Sec. 3.2): 100k vs 1M, 10,000 shuffles per launch --
+    # ================= Monte-Carlo significance test (config of Table 1) ========
     g3, a3_np, b3_np = bits_synth.config3()
     co_np, cl_np = bits_synth.mc_contig_table(g3)
     db3 = bits.Database(to_dev(b3_np), rmi_leaves_log2=16)
     a3, co, cl = to_dev(a3_np), to_dev(co_np), to_dev(cl_np)
     n_sh = 10_000
-    totals3 = torch.empty(n_sh, dtype=torch.uint64, device=dev)
+    s0, s1 = sharding.shuffle_range(n_sh, rank, world)
+    totals3 = torch.empty(max(s1 - s0, 1), dtype=torch.uint64, device=dev)
     mc_forms = {}
-    mc_out = None
+    mc_windows = {}
+    gobs, gk, _, gtot = goldens.read_mc_fullsize()
     for name, m in (("search", bits.METHOD_SEARCH), ("rmi", bits.METHOD_RMI)):
-        res = []
-
-        def mc_step(m=m, res=res):
-            res.append(db3.mc(a3, co, cl, seed=7, shuffle_end=n_sh, totals=totals3, method=m))
+        def mc_step(m=m):
+            db3.mc(a3, co, cl, seed=7, shuffle_begin=s0, shuffle_end=s1, totals=totals3, method=m)
 
         ms, l, win = timed(mc_step, args.steps, args.warmup)
-        if name == "search":
-            mc_window = win
-        mc_forms[name] = {"ms_per_step": ms, "shuffles_per_s": world * n_sh / (ms * 1e-3),
-                          "placements_per_s": world * n_sh * a3_np.shape[0] / (ms * 1e-3),
+        mc_windows[name] = win
+        mc_forms[name] = {"ms": ms, "shuffles_per_s": n_sh / (ms * 1e-3),
+                          "placements_per_s": n_sh * a3_np.shape[0] / (ms * 1e-3),
                           "gpu_launches": l}
-        mc_out = res[-1][1:]
-    t3 = totals3.cpu().numpy()
-    bs3, be3 = o.build(b3_np)
-    mc_parity = all(int(t3[s]) == int(o.mc(a3_np, co_np, cl_np, bs3, be3, seed=7, s_begin=s,
-                                           s_end=s + 1)[0][0]) for s in (0, 4999, 9999))
-    best_mc = min(mc_forms.values(), key=lambda f: f["ms_per_step"])
-    # The MC kernel is bound by instruction issue (its database stays in L2):
-    # roofline = warp instructions issued per second against one warp
-    # instruction per clock per scheduler (148 SMs x 4) at the sampled clock.
+        if dist is not None:
+            tot, st = sharding.sharded_mc(db3, a3, co, cl, seed=7, n_shuffles=n_sh, method=m)
+            t_all, k_all, obs_all = tot.cpu().numpy(), st["k_ge"], st["observed"]
+        else:
+            _, obs_all, k_all, _ = db3.mc(a3, co, cl, seed=7, shuffle_end=n_sh, totals=totals3,
+                                          method=m)
+            t_all = totals3.cpu().numpy()
+        parity[f"mc_{name}_all_10000_totals"] = bool(
+            np.array_equal(t_all, gtot) and obs_all == gobs and k_all == gk)
+    best_mc = min(mc_forms, key=lambda k: mc_forms[k]["ms"])
     mc_src = ["paper_1208_3407_b300/csrc/mc.cu", "paper_1208_3407_b300/csrc/mc_unit.cuh",
               "paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/philox.cuh"]
     wi = profiled_value("k_mc_search", "warp_instructions_per_launch", mc_src)
-    mc_roof = None  # filled in once the clock samples of its timed window are in
     nodes_pp = 2 * tree_levels(b3_np.shape[0])
-    mc_l2 = {"bound": "L2 random 64-B node reads", "kernel": "k_mc_search<false>",
-             "achieved": nodes_pp * n_sh * a3_np.shape[0] / (mc_forms["search"]["ms_per_step"] * 1e-3),
-             "peak": l2_peak, "unit": "nodes/s", "nodes_per_placement": nodes_pp,
-             "peak_source": "bits_probe_random_reads on a 32 MiB (L2-resident) buffer in this "
-                            "run, best of three"}
+    mc_l2 = {"bound": "random 64-B node reads from L2 (probe, 32 MiB)",
+             "achieved": nodes_pp * n_sh * a3_np.shape[0] / (mc_forms["search"]["ms"] * 1e-3),
+             "peak": l2_peak, "unit": "nodes/s", "nodes_per_placement": nodes_pp}
     mc_l2["frac"] = mc_l2["achieved"] / l2_peak
-    mc = {"workload": "100,000 uniform intervals (len U[100,2000]) vs 1,000,000 clustered "
-                      "(200,000 hotspots) on the 24-contig genome, 10,000 shuffles, seed 7",
-          "shuffles_per_s": best_mc["shuffles_per_s"], "forms": mc_forms, "roofline": mc_roof,
-          "roofline_l2": mc_l2,
-          "observed": mc_out[0], "k_ge": mc_out[1], "p_value": mc_out[2],
-          "parity_sample_ok": bool(mc_parity),
-          "paper_context": "Table 1: BITS-CUDA, size 1e5, 10,000 rounds in 28 s "
-                           "(357 shuffles/s) on an unnamed 2012 GPU"}
     db3.free()
     del a3, co, cl, totals3
 
-    # ---- learned index at scale: 100M queries vs 100M intervals ----------------
-    a4_np, b4_np = bits_synth.config4()
-    b4 = to_dev(b4_np)
-    t0 = time.time()
-    db4 = bits.Database(b4, rmi_leaves_log2=16)
-    torch.cuda.synchronize()
-    build4_s = time.time() - t0
-    del b4
-    a4 = to_dev(a4_np)
-    c4 = torch.empty(a4_np.shape[0], dtype=torch.uint32, device=dev)
-    t4 = torch.empty(1, dtype=torch.uint64, device=dev)
-    scale_forms = {}
-    steps4 = max(3, min(args.steps, 5))
-    totals4 = {}
-    for name, m, per_query in (("search", bits.METHOD_SEARCH, True),
-                               ("rmi", bits.METHOD_RMI, True),
-                               ("mergepath", bits.METHOD_MERGEPATH, True),
-                               ("search_total_only", bits.METHOD_SEARCH, False),
-                               ("mergepath_total_only", bits.METHOD_MERGEPATH, False)):
-        out_c = c4 if per_query else False
-        ms, _, _ = timed(lambda m=m, out_c=out_c: db4.count(a4, counts=out_c, total=t4, method=m,
-                                                            check=False), steps4, 3)
-        totals4[name] = int(t4.cpu().numpy()[0])
-        scale_forms[name] = {"ms_per_step": ms,
-                             "queries_per_s": world * a4_np.shape[0] / (ms * 1e-3)}
-    db4.check()
-    assert len(set(totals4.values())) == 1, totals4
-    idx4 = np.random.default_rng(2).choice(a4_np.shape[0], size=16, replace=False)
-    oc4, _ = o.count_brute(a4_np[idx4], b4_np)
-    for f in scale_forms.values():
-        f["level0_node_reads_per_s"] = world * 2 * a4_np.shape[0] / (f["ms_per_step"] * 1e-3)
-    scale = {"workload": "100,000,000 uniform queries vs 100,000,000 intervals from 1000 "
-                         "Gaussians + 20% uniform on a 3.0 Gbp line, lengths log-uniform "
-                         "[50, 10^4], learned index with 2^16 linear leaves per array",
-             "forms": scale_forms, "build_with_learned_index_s": build4_s,
-             "roofline_random_access": {
-                 "bound": "hbm random 64-B node reads (independent, uniform over 4 GiB)",
-                 "kernel": "k_count_search",
-                 "achieved": scale_forms["search"]["level0_node_reads_per_s"] / world,
-                 "peak": rand_peak, "unit": "nodes/s",
-                 "frac": scale_forms["search"]["level0_node_reads_per_s"] / world / rand_peak,
-                 "nodes_per_query": 2,
-                 "note": "above 1: with the levels interleaved by node a query's two level-0 "
-                         "reads, over an 800 MB region, are served faster than two independent "
-                         "random reads over 4 GiB"},
-             "parity_sample_ok": bool(np.array_equal(c4.cpu().numpy()[idx4], oc4))}
-    db4.free()
-    del a4, c4
-
-    # ---- all-pairs screen (Sec. 3.3): 64 query sets x 32 databases -------------
-    g5, a5_np, b5_np = bits_synth.config5()
-    t0 = time.time()
-    dbs5 = [bits.Database(to_dev(b5), rmi_leaves_log2=16) for b5 in b5_np]
-    torch.cuda.synchronize()
-    build5_s = time.time() - t0
-    a5 = [to_dev(x) for x in a5_np]
-    m5 = torch.empty((len(a5), len(dbs5)), dtype=torch.uint64, device=dev)
-    bits.count_matrix(dbs5, a5, out=m5)          # autotunes and captures the graph
-    steps5 = max(3, min(args.steps, 5))
-    ms5, l5, _ = timed(lambda: bits.count_matrix(dbs5, a5, out=m5), steps5, 3)
-    m5_np = m5.cpu().numpy()
-    n_q5 = sum(x.shape[0] for x in a5_np)
-    checks = []
-    for (i, j) in ((0, 0), (int(np.argmin([x.shape[0] for x in a5_np])), 31)):
-        t = dbs5[j].count(a5[i], counts=False, method=bits.METHOD_SEARCH)[1]
-        checks.append(int(t.cpu().numpy()[0]) == int(m5_np[i, j]))
-    i_small = int(np.argmin([x.shape[0] for x in a5_np]))
-    bs5, be5 = o.build(b5_np[5])
-    checks.append(o.count_sorted(a5_np[i_small], bs5, be5, want_counts=False)[1] ==
-                  int(m5_np[i_small, 5]))
-    ap_nodes = sum(x.shape[0] * 2 * tree_levels(b5.shape[0]) for x in a5_np for b5 in b5_np)
-    ap_l2 = {"bound": "L2 random 64-B node reads", "kernel": "k_allpairs",
-             "achieved": ap_nodes / (ms5 * 1e-3), "peak": l2_peak, "unit": "nodes/s",
-             "frac": ap_nodes / (ms5 * 1e-3) / l2_peak,
-             "nodes_per_pair": ap_nodes / (n_q5 * len(b5_np)),
-             "note": "2 node reads per search per tree level below the shared-memory top; "
-                     "the level-0 reads of the databases larger than L2 come from DRAM"}
-    allpairs = {"workload": "64 query sets x 32 databases on the 24-contig genome, sizes "
-                            "log-uniform [1e3, 2e7] (seed 11), lengths U[50,5000], even sets "
-                            "clustered, one learned index per database",
-                "ms_per_step": ms5, "pairs": len(a5) * len(dbs5),
-                "query_database_counts_per_s": world * n_q5 * len(dbs5) / (ms5 * 1e-3),
-                "queries_total": n_q5, "gpu_launches": l5, "build_32_databases_s": build5_s,
-                "roofline_l2": ap_l2,
-                "parity_sample_ok": bool(all(checks)),
-                "paper_context": "Sec. 3.3: 159 x 159 tracks, about 4e9 intervals per iteration, "
-                                 "9,069 minutes for 1e4 iterations on one 2012 GPU"}
-    # ---- Monte-Carlo screen (Sec. 3.3): every pair re-placed and recounted ----
-    # The same 64 x 32 sets, 4 shuffles of every query set per step against
-    # all 32 databases (1.4e10 placements); the paper's screen ran 1e4.
-    co5, cl5 = bits_synth.mc_contig_table(g5)
-    dco5, dcl5 = to_dev(co5), to_dev(cl5)
-    nsh5 = 4
-    scr_out = (torch.empty((len(a5), len(dbs5)), dtype=torch.uint64, device=dev),
-               torch.empty((len(a5), len(dbs5), nsh5), dtype=torch.uint64, device=dev),
-               torch.empty((len(a5), len(dbs5), 8), dtype=torch.uint64, device=dev))
-
-    def screen_step():
-        bits.mc_matrix(dbs5, a5, dco5, dcl5, seed=17, shuffle_end=nsh5, out=scr_out)
-
-    screen_step()                                  # builds and caches the launch graph
-    ms_scr, l_scr, scr_window = timed(screen_step, 3, 3)
-    for d in dbs5:
-        d.check()
-    i_s = int(np.argmin([x.shape[0] for x in a5_np]))
-    bs5, be5 = o.build(b5_np[7])
-    ot, oo, _, _ = o.mc(a5_np[i_s], co5, cl5, bs5, be5, seed=17, s_begin=0, s_end=nsh5,
-                        threads=os.cpu_count() or 1, set_index=i_s)
-    scr_ok = bool(np.array_equal(scr_out[1][i_s, 7].cpu().numpy(), ot) and
-                  int(scr_out[0][i_s, 7].cpu()) == oo)
-    placements = n_q5 * len(dbs5) * nsh5
-    # Issue-bound like the single test: warp instructions per placement from
-    # the ncu capture of the 16 x 8 screen, times this step's placements.
-    mm_src = ["paper_1208_3407_b300/csrc/mc_matrix.cu", "paper_1208_3407_b300/csrc/mc_unit.cuh",
-              "paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/philox.cuh"]
-    wi_m = profiled_value("k_mc_matrix_screen_16x8", "warp_instructions_per_launch", mm_src)
-    pl_m = profiled_value("k_mc_matrix_screen_16x8", "placements_per_launch", mm_src)
-    scr_roof = None  # filled in once the clock samples of its timed window are in
-    scr_nodes = sum(x.shape[0] * nsh5 * 2 * tree_levels(b5.shape[0])
-                    for x in a5_np for b5 in b5_np)
-    scr_l2 = {"bound": "L2 random 64-B node reads", "kernel": "k_mc_matrix",
-              "achieved": world * scr_nodes / (ms_scr * 1e-3), "peak": l2_peak, "unit": "nodes/s",
-              "nodes_per_placement": scr_nodes / placements,
-              "note": "2 node reads per search per tree level below the shared-memory top of "
-                      "each database; the largest databases also read level 0 from DRAM"}
-    scr_l2["frac"] = scr_l2["achieved"] / world / l2_peak
-    mc_screen = {"workload": "the all-pairs sets above, 4 shuffles per step of every query set "
-                             "against all 32 databases, plus the observed matrix and per-pair "
-                             "summary (tallies, median, Fig. 3 score)",
-                 "ms_per_step": ms_scr, "shuffles_per_step": nsh5,
-                 "placements_per_s": world * placements / (ms_scr * 1e-3),
-                 "pair_shuffles_per_s": world * len(a5) * len(dbs5) * nsh5 / (ms_scr * 1e-3),
-                 "gpu_launches": l_scr, "parity_sample_ok": scr_ok, "roofline": scr_roof,
-                 "roofline_l2": scr_l2,
-                 "paper_context": "Sec. 3.3: 1e4 shuffles of the 159 x 159 screen in 9,069 "
-                                  "minutes on one 2012 GPU"}
-    for d in dbs5:
-        d.free()
-    del a5, m5, scr_out
-
+    # ================= rank 0 only: the other workloads ==========================
+    sections = {}
+    if lead:
+        sections = other_workloads(args, bits, bits_synth, goldens, o, torch, dev, to_dev,
+                                   timed, flush, stream, hbm_peak, l2_peak, parity, detail)
     sampler.stop()
 
-    # Instruction-issue rooflines of the Monte-Carlo kernels, at the SM clock
-    # sampled during their own timed windows (long, busy phases of the run,
-    # unlike the microsecond headline steps).
-    def issue_roofline(warp_instr, ms, window, kernel, note):
+    def issue_roofline(warp_instr, ms, window):
         ck = sampler.summary(*window)
         mhz = ck.get("sm_mhz") or clocks.get("sm_mhz")
         if warp_instr is None or not mhz:
@@ -630,102 +515,209 @@ def run_ours(args):
         peak = 148 * 4 * mhz * 1e6
         ach = warp_instr / (ms * 1e-3)
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "warp-instructions/s",
-                "frac": ach / peak, "kernel": kernel, "clocks": ck,
-                "peak_source": "148 SMs x 4 schedulers x 1 warp-instruction/clock at the SM "
-                               "clock sampled during this workload's timed steps" + note}
+                "frac": ach / peak, "sm_mhz": mhz}
 
-    mc["roofline"] = issue_roofline(wi, mc_forms["search"]["ms_per_step"], mc_window,
-                                    "k_mc_search<false>", "")
-    if wi_m is not None and pl_m:
-        mc_screen["roofline"] = issue_roofline(wi_m / pl_m * placements, ms_scr, scr_window,
-                                               "k_mc_matrix",
-                                               "; instructions per placement from the 16 x 8 "
-                                               "capture")
+    mc_issue = issue_roofline(wi, mc_forms["search"]["ms"], mc_windows["search"])
 
-    # ---- CPU baseline: the oracle as it stands, on a bounded sample -----------
-    cpu = None
-    if rank == 0:
-        bs_np, be_np = o.build(b_np)
-        cores = os.cpu_count() or 1
-        sample = a_np[:100_000]
-        t = time.perf_counter()
-        reps = 0
-        while True:
-            o.count_sorted(sample, bs_np, be_np, threads=cores)
-            reps += 1
-            if time.perf_counter() - t > 5.0:
-                break
-        cpu_s = (time.perf_counter() - t) / reps
-        cpu = {"value": sample.shape[0] / cpu_s, "unit": "queries/s", "cores": cores,
-               "kind": "oracle",
-               "sample": f"first 100,000 of the 200,000 queries x {reps} repetitions, "
-                         "database sorted beforehand (std::sort), std::thread over all cores"}
+    # ================= CPU baseline: the oracle protocol ==========================
+    cpu = proto = None
+    if lead:
+        proto = oracle_protocol(o, a4_np, b4_np, bs4, be4, cores)
+        cpu = cpu_baseline_from(proto)
 
-    # Roofline of the headline's kernel: algorithmic bytes per query = 8 B query
-    # read + 4 B count write + one 32 B sector per search of an array larger
-    # than L2 (two searches per query) = 76 B.
-    kernel = "k_count_rmi" if auto_method == "rmi" else "k_count_search"
-    achieved = 76.0 * n_a / (head_ms * 1e-3) / 1e9
-    src = (["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/rmi_search.cuh",
-            "paper_1208_3407_b300/csrc/rmi.cu"] if auto_method == "rmi" else
-           ["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/count.cu"])
-    traffic = profiled_traffic(kernel, src)
+    value = n4 / (head_ms * 1e-3)
     line = {
-        "metric": METRIC, "value": world * n_a / (head_ms * 1e-3), "unit": "queries/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head_ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic (seeded generator; the paper's alignment and exon datasets are "
-                "not available)",
-        "config": {"workload": HEADLINE,
-                   "method": f"{head} (the faster of plain search and learned index, both timed here)",
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicated database, {world} rank(s), no collective"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": kernel, "algorithmic_bytes_per_query": 76},
-        "roofline_random_access": {
-            "bound": "hbm random 64-B node reads (independent, uniform over 4 GiB)",
-            "kernel": kernel, "achieved": 2.0 * n_a / (head_ms * 1e-3), "peak": rand_peak,
-            "unit": "nodes/s", "frac": 2.0 * n_a / (head_ms * 1e-3) / rand_peak,
-            "nodes_per_query": 2,
-            "peak_source": "bits_probe_random_reads in this run: quads reading random 64-byte "
-                           "nodes of a 4 GiB buffer with a 64-byte line fill, best of three",
-            "note": "each search of an array larger than L2 reads one level-0 node from DRAM; "
-                    "the step time also holds the fixed cost of a cold launch (about 10 us "
-                    "even for one query)"},
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head_ms,
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded generator; the paper's datasets are not available)",
+        "config": config_dict(world),
+        "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * n_a / (e2e_ms * 1e-3), "unit": "queries/s",
-                "h2d_bytes_per_step": int(a_np.nbytes), "d2h_bytes_per_step": int(n_a * 4 + 8),
-                "ms_per_step": e2e_ms, "gpu_launches": e2e_launches, "parity_ok": e2e_ok,
-                "call": "bits_count_host: page-locked queries read and counts written in place "
-                        "by the search kernel over the bus, the total copied back; the timed "
-                        "region ends with an event after the call on its stream",
-                "staged_copies": {"value": world * n_a / (e2e_staged_ms * 1e-3),
-                                  "ms_per_step": e2e_staged_ms,
-                                  "call": "torch H2D copy, bits_count on device buffers, "
-                                          "D2H copies of counts and total"}},
+        "e2e": {"value": n4 / (e2e_ms * 1e-3), "unit": "queries/s",
+                "h2d_bytes_per_step": int(n4 * 8), "d2h_bytes_per_step": int(n4 * 4 + 8),
+                "ms_per_step": e2e_ms, "gpu_launches": e2e_launches,
+                "call": "bits_count_host on page-locked queries and counts (read and written in "
+                        "place by the search kernel over the bus) + the total copied back"},
         "gpu_launches": launches,
         "clocks": clocks,
-        "forms": forms,
-        "one_shot": {"ms_per_step": one_ms, "queries_per_s": world * n_a / (one_ms * 1e-3),
-                     "gpu_launches": one_launches,
-                     "call": "bits_build_db of the 20M reads (radix sort of B_S and B_E, tree "
-                             "levels) + bits_count of the 200k queries + bits_free, per step"},
-        "build": {"ms": build_ms, "intervals": n_b, "intervals_per_s": n_b / (build_ms * 1e-3),
-                  "gpu_launches": build_launches,
-                  "with_learned_index_s": build_rmi_s},
-        "parity_sample_ok": parity_ok,
-        "project": project,
-        "enumerate": enumerate_,
-        "mc": mc,
-        "scale": scale,
-        "allpairs": allpairs,
-        "mc_screen": mc_screen,
+        "headline_form": head,
+        "roofline_random_access": sig(random_access),
+        "probe": sig({"dram_nodes_per_s": rand_peak, "l2_nodes_per_s": l2_peak}),
     }
-    if rank == 0:
+    line.update(sig(sections))
+    line["build_100m_ms"] = sig({"plain": statistics.fmean(t for r, t in build4 if not r),
+                                 "with_learned_index": statistics.fmean(t for r, t in build4 if r)})
+    line["protocol"] = sig(proto) if proto else None
+    line["forms"] = sig({k: {"ms": v["ms"], "qps": v["queries_per_s"]} for k, v in forms.items()})
+    line["mc"] = sig({
+        "workload": "100k x 1M, 10,000 shuffles per launch (Table 1 corner)",
+        "shuffles_per_s": mc_forms[best_mc]["shuffles_per_s"],
+        "placements_per_s": mc_forms[best_mc]["placements_per_s"], "form": best_mc,
+        "forms": {k: {"ms": v["ms"], "shuffles_per_s": v["shuffles_per_s"]}
+                  for k, v in mc_forms.items()},
+        "roofline_l2_frac": mc_l2["frac"],
+        "roofline_issue_frac": mc_issue["frac"] if mc_issue else None,
+        "paper": "357 shuffles/s (Table 1, 1e5 x 1e4, 2012 GPU)"})
+    line["parity"] = parity
+    detail.update({"line": line, "forms_full": forms, "mc_forms": mc_forms, "mc_l2": mc_l2,
+                   "mc_issue": mc_issue, "protocol": proto, "build4": build4})
+    if lead:
+        if args.detail:
+            with open(args.detail, "w") as f:
+                json.dump(detail, f, indent=1, default=str)
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def other_workloads(args, bits, bits_synth, goldens, o, torch, dev, to_dev, timed, flush, stream,
+                    hbm_peak, l2_peak, parity, detail):
+    """Exome-vs-reads count forms, build, one-shot, host buffers, projection and
+    enumeration; the 10k x 10k count; the 64 x 32 all-pairs count and screen."""
+    out = {}
+    # ---- 10,000 x 10,000 on one 1 Mbp contig (launch-bound) -------------------
+    a1_np, b1_np = bits_synth.config1()
+    db1 = bits.Database(to_dev(b1_np))
+    a1 = to_dev(a1_np)
+    c1 = torch.empty(a1_np.shape[0], dtype=torch.uint32, device=dev)
+    t1 = torch.empty(1, dtype=torch.uint64, device=dev)
+    ms1, _, _ = timed(lambda: db1.count(a1, counts=c1, total=t1, method=bits.METHOD_SEARCH,
+                                        check=False), args.steps, args.warmup, all_ranks=False)
+    oc1, _ = o.count_brute(a1_np, b1_np)
+    parity["small_10k_brute_force"] = bool(np.array_equal(c1.cpu().numpy(), oc1))
+    db1.free()
+    out["small_10k_us"] = ms1 * 1e3
+
+    # ---- exome-vs-reads: 200,000 queries vs 20,000,000 reads ------------------
+    genome, a_np, b_np = bits_synth.config2()
+    n_a, n_b = a_np.shape[0], b_np.shape[0]
+    a, b = to_dev(a_np), to_dev(b_np)
+    builds = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d = bits.Database(b)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            builds.append(e0.elapsed_time(e1))
+        d.free()
+    build_ms = statistics.fmean(builds)
+    one_c = torch.empty(n_a, dtype=torch.uint32, device=dev)
+    one_t = torch.empty(1, dtype=torch.uint64, device=dev)
+
+    def one_shot():
+        d = bits.Database(b)
+        d.count(a, counts=one_c, total=one_t, method=bits.METHOD_SEARCH, check=False)
+        d.free()
+
+    one_ms, _, _ = timed(one_shot, args.steps, args.warmup, all_ranks=False)
+    db = bits.Database(b, rmi_leaves_log2=16)
+    counts = torch.empty(n_a, dtype=torch.uint32, device=dev)
+    total = torch.empty(1, dtype=torch.uint64, device=dev)
+    ex_forms = {}
+    for name, m in (("search", bits.METHOD_SEARCH), ("rmi", bits.METHOD_RMI)):
+        ms, _, _ = timed(lambda m=m: db.count(a, counts=counts, total=total, method=m,
+                                              check=False), args.steps, args.warmup,
+                         all_ranks=False)
+        ex_forms[name] = ms
+    db.check()
+    idx = np.random.default_rng(0).choice(n_a, size=256, replace=False)
+    oc, _ = o.count_brute(a_np[idx], b_np)
+    parity["exome_counts_256_brute_force"] = bool(np.array_equal(counts.cpu().numpy()[idx], oc))
+    a_host = torch.from_numpy(a_np.astype(np.uint32)).pin_memory()
+    ch = torch.zeros(n_a, dtype=torch.uint32).pin_memory()
+    th = torch.zeros(1, dtype=torch.uint64).pin_memory()
+    host_ms, _, _ = timed(lambda: db.count_host(a_host, counts=ch, total=th,
+                                                method=bits.METHOD_SEARCH, check=False),
+                          args.steps, args.warmup, all_ranks=False)
+    db.free()
+    ex = {"count_us": {k: v * 1e3 for k, v in ex_forms.items()},
+          "count_qps": n_a / (min(ex_forms.values()) * 1e-3),
+          "host_buffers_us": host_ms * 1e3, "build_20m_ms": build_ms,
+          "build_keys_per_s": 2 * n_b / (build_ms * 1e-3),
+          "one_shot_ms": one_ms}
+
+    # projection of 20M chromosome-local closed reads (12 B read + 8 B written each)
+    pc_np, ps_np, pe_np = bits_synth.local_intervals(genome, n_b, seed=5, lo=100, hi=100,
+                                                     closed=True)
+    pc, ps, pe = to_dev(pc_np), to_dev(ps_np), to_dev(pe_np)
+    pco, pcl = to_dev(genome.offsets), to_dev(genome.lengths)
+    p_out = torch.empty((n_b, 2), dtype=torch.uint32, device=dev)
+    proj_ms, _, _ = timed(lambda: bits.project(ps, pe, contig=pc, contig_off=pco, contig_len=pcl,
+                                               closed=True, out=p_out),
+                          args.steps, args.warmup, all_ranks=False)
+    pidx = np.random.default_rng(1).choice(n_b, size=4096, replace=False)
+    exp_p, _ = o.project(pc_np[pidx], ps_np[pidx], pe_np[pidx], genome.offsets, genome.lengths,
+                         closed=True)
+    parity["projection_4096_sample"] = bool(np.array_equal(p_out.cpu().numpy()[pidx], exp_p))
+    ex["project_ms"] = proj_ms
+    ex["project_hbm_frac"] = 20.0 * n_b / (proj_ms * 1e-3) / 1e9 / hbm_peak
+    del pc, ps, pe, p_out
+
+    # enumeration of every intersecting pair
+    db_en = bits.Database(b, enumerate=True)
+    en_ms, _, _ = timed(lambda: db_en.enumerate(a, check=False), args.steps, args.warmup,
+                        all_ranks=False)
+    off_g, pairs_g = db_en.enumerate(a)
+    eidx = np.random.default_rng(2).choice(n_a, size=64, replace=False)
+    eoff, epairs = o.enumerate_scan(a_np[eidx], b_np)
+    off_np, pairs_np = off_g.cpu().numpy(), pairs_g.cpu().numpy()
+    ok = True
+    for k, i in enumerate(eidx):
+        ok &= bool(np.array_equal(pairs_np[int(off_np[i]):int(off_np[i + 1]), 1],
+                                  epairs[int(eoff[k]):int(eoff[k + 1]), 1]))
+    parity["enumeration_64_queries"] = ok
+    ex["enumerate_ms"] = en_ms
+    ex["enumerate_pairs_per_s"] = int(off_np[-1]) / (en_ms * 1e-3)
+    db_en.free()
+    del off_g, pairs_g, a, b
+    out["exome"] = ex
+
+    # ---- all-pairs: 64 query sets x 32 databases ------------------------------
+    g5, a5_np, b5_np = bits_synth.config5()
+    dbs5 = [bits.Database(to_dev(x), rmi_leaves_log2=16) for x in b5_np]
+    a5 = [to_dev(x) for x in a5_np]
+    m5 = torch.empty((len(a5), len(dbs5)), dtype=torch.uint64, device=dev)
+    bits.count_matrix(dbs5, a5, out=m5)          # autotunes and captures the graph
+    ms5, _, _ = timed(lambda: bits.count_matrix(dbs5, a5, out=m5), max(3, min(args.steps, 5)), 3,
+                      all_ranks=False)
+    parity["allpairs_all_2048_totals"] = bool(np.array_equal(m5.cpu().numpy(),
+                                                             goldens.read_allpairs_fullsize()))
+    n_q5 = sum(x.shape[0] for x in a5_np)
+    ap_nodes = sum(x.shape[0] * 2 * tree_levels(y.shape[0]) for x in a5_np for y in b5_np)
+    out["allpairs"] = {"ms": ms5, "pair_counts_per_s": n_q5 * len(dbs5) / (ms5 * 1e-3),
+                       "roofline_l2_frac": ap_nodes / (ms5 * 1e-3) / l2_peak}
+    # ---- Monte-Carlo screen over the same sets: 4 shuffles per step -------------
+    co5, cl5 = bits_synth.mc_contig_table(g5)
+    dco5, dcl5 = to_dev(co5), to_dev(cl5)
+    nsh5 = 4
+    scr = (torch.empty((len(a5), len(dbs5)), dtype=torch.uint64, device=dev),
+           torch.empty((len(a5), len(dbs5), nsh5), dtype=torch.uint64, device=dev),
+           torch.empty((len(a5), len(dbs5), 8), dtype=torch.uint64, device=dev))
+
+    def screen_step():
+        bits.mc_matrix(dbs5, a5, dco5, dcl5, seed=17, shuffle_end=nsh5, out=scr)
+
+    screen_step()
+    ms_scr, _, _ = timed(screen_step, 3, 3, all_ranks=False)
+    for d in dbs5:
+        d.check()
+    i_s = int(np.argmin([x.shape[0] for x in a5_np]))
+    bs5, be5 = o.build(b5_np[7])
+    ot, oo, _, _ = o.mc(a5_np[i_s], co5, cl5, bs5, be5, seed=17, s_begin=0, s_end=nsh5,
+                        threads=os.cpu_count() or 1, set_index=i_s)
+    parity["screen_sample_pair"] = bool(np.array_equal(scr[1][i_s, 7].cpu().numpy(), ot) and
+                                        int(scr[0][i_s, 7].cpu()) == oo)
+    out["mc_screen"] = {"ms": ms_scr,
+                        "placements_per_s": n_q5 * len(dbs5) * nsh5 / (ms_scr * 1e-3)}
+    for d in dbs5:
+        d.free()
+    detail["other"] = out
+    return out
 
 
 def main():
@@ -734,6 +726,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--detail", default=None, help="also write every measured number here")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

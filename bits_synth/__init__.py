@@ -9,8 +9,8 @@ own.
 Every interval set is returned as an ``(n, 2)`` ``numpy.uint32`` array in
 array-of-structures order ``[[start, end], ...]`` with half-open ``[start,
 end)`` semantics, already projected onto one genome-wide coordinate line by
-adding each contig's offset (the projection of the paper's Sec. 2.3,
-"The BITS solution to the counting problem").
+adding each contig's offset (the projection paragraph of the paper's Sec.
+"BITS Algorithm", "The BITS solution to the counting problem").
 
 Workload shapes (the paper's datasets are not available, so these stand in):
 
@@ -19,8 +19,9 @@ Workload shapes (the paper's datasets are not available, so these stand in):
                  drawn 70 % from 200k Gaussian hotspots.
 * ``config3``    Monte-Carlo significance shape (Table 1's 1e5/1e6 corner).
 * ``config4``    learned-index scale: 100M x 100M on a 3.0 Gbp line.
-* ``config5``    all-pairs screen shape (Sec. 3.3): 64 query sets x 32
-                 database sets of log-uniform size.
+* ``config5``    all-pairs screen shape (Sec. "Novel genomic
+                 relationships"): 64 query sets x 32 database sets of
+                 log-uniform size.
 """
 from __future__ import annotations
 

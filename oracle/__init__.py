@@ -111,7 +111,8 @@ class Oracle:
         return counts, int(total[0])
 
     def count_brute_closed(self, a, b):
-        """Sec. 1.1's closed predicate, by brute force (intervals [start, end])."""
+        """The closed predicate of Sec. "Interval Set Intersection problem", by
+        brute force (intervals [start, end])."""
         a, b = _iv(a), _iv(b)
         counts = np.zeros(a.shape[0], np.uint32)
         total = np.zeros(1, np.uint64)
@@ -121,8 +122,8 @@ class Oracle:
         return counts, int(total[0])
 
     def project(self, chrom, start, end, contig_off=None, contig_len=None, closed=False):
-        """Sec. 2.3 projection; returns (intervals, number rejected).  Rejected rows
-        are (2^32 - 1, 0).  With no contig table the line is one contig at 0."""
+        """The projection of Sec. "BITS Algorithm"; returns (intervals, number
+        rejected).  Rejected rows are (2^32 - 1, 0).  With no contig table the line is one contig at 0."""
         start = np.ascontiguousarray(start, np.uint32)
         end = np.ascontiguousarray(end, np.uint32)
         n = start.shape[0]
@@ -217,7 +218,8 @@ class Oracle:
         return totals, int(obs[0]), int(k[0]), p.value
 
     def mc_summary(self, totals, observed: int) -> dict:
-        """Tally, middles and enrichment score of one MC test (Sec. 3.2, Fig. 3)."""
+        """Tally, middles and enrichment score of one MC test (Sec. "Monte Carlo
+        Simulations", Fig. 3)."""
         t = np.ascontiguousarray(totals, np.uint64)
         ints = np.zeros(5, np.uint64)
         dbl = (C.c_double * 3)()

@@ -7,16 +7,17 @@
 //
 // Conventions (the readings of the paper this oracle follows):
 //   * intervals are half-open [start, end) uint32 pairs, so a and b intersect
-//     iff b.start < a.end and b.end > a.start (the paper's Sec. 1.1 predicate
-//     written for half-open intervals);
+//     iff b.start < a.end and b.end > a.start (the paper's Sec. "Interval Set
+//     Intersection problem" predicate written for half-open intervals);
 //   * database intervals must be non-empty (start < end); queries may be
 //     empty (start == end) but not inverted (end < start);
-//   * self-intersections inside A or inside B are never counted (Sec. 1.1);
+//   * self-intersections inside A or inside B are never counted (Sec.
+//     "Interval Set Intersection problem");
 //   * ICount (Algorithm 1) uses counts, not indices:
 //       first = #{ e in B_S : e <  a.end   }   (lower bound of a.end)
 //       last  = #{ e in B_E : e <= a.start }   (upper bound of a.start)
 //       c     = first - last
-//   * Monte-Carlo (Sec. 3.2): A is re-placed, B stays fixed.  Interval i of
+//   * Monte-Carlo (Sec. "Monte Carlo Simulations"): A is re-placed, B stays fixed.  Interval i of
 //     shuffle s draws Philox4x32-10 with counter (i, s, 0, 0) and key
 //     (seed low word, seed high word); u = x1 * 2^32 + x0; its new start is
 //     off[c] + floor(u * (len[c] - len_i + 1) / 2^64) inside its own contig c,
@@ -52,7 +53,7 @@ void parallel_ranges(uint64_t n, int threads, F f) {
   for (auto& th : pool) th.join();
 }
 
-// Intersection predicate of Sec. 1.1, half-open form.
+// Intersection predicate of Sec. "Interval Set Intersection problem", half-open form.
 inline bool intersects(uint32_t as, uint32_t ae, uint32_t bs, uint32_t be) {
 #ifdef ORACLE_MUTANT_CLOSED
   return bs <= ae && be >= as;  // planted mistake: the closed-interval predicate
@@ -138,8 +139,9 @@ inline int64_t contig_of(const uint32_t* coff, uint32_t nc, uint32_t pos) {
 
 extern "C" {
 
-// Brute force over all |A||B| pairs: the definition of Sec. 1.1 directly.
-// counts (nullable) gets |I(B, a_i)|, total gets the size of I(A, B).
+// Brute force over all |A||B| pairs: the definition of Sec. "Interval Set
+// Intersection problem" directly. counts (nullable) gets |I(B, a_i)|, total
+// gets the size of I(A, B).
 int or_count_brute(const uint32_t* a, uint64_t na, const uint32_t* b, uint64_t nb,
                    uint32_t* counts, uint64_t* total) {
   if (check_db(b, nb) || check_queries(a, na)) return 1;
@@ -195,12 +197,13 @@ void or_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
 
 uint64_t or_scale_u64(uint64_t u, uint64_t n) { return scale_u64(u, n); }
 
-// New placement of every A interval for shuffle s (Sec. 3.2 null model).
+// New placement of every A interval for shuffle s (Sec. "Monte Carlo Simulations" null model).
 // out receives [start, end) pairs.  Returns 1 if an interval is inverted,
 // lies outside every contig, or crosses its contig's end.  `set` is the
-// index of the query set in a screen of many sets (Sec. 3.3): interval i of
-// set `set` in shuffle s draws the Philox block at counter (i, s, set, 0), so
-// every set has its own stream and a single test is set 0.
+// index of the query set in a screen of many sets (Sec. "Novel genomic
+// relationships"): interval i of set `set` in shuffle s draws the Philox block
+// at counter (i, s, set, 0), so every set has its own stream and a single test
+// is set 0.
 int or_mc_place_set(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* clen,
                     uint32_t nc, uint64_t seed, uint32_t s, uint32_t set, uint32_t* out) {
   const uint32_t key[2] = {uint32_t(seed), uint32_t(seed >> 32)};
@@ -232,7 +235,7 @@ int or_mc_place_set(const uint32_t* a, uint64_t na, const uint32_t* coff, const 
   return 0;
 }
 
-// Monte-Carlo significance test (Sec. 3.2): totals[s - s_begin] for each
+// Monte-Carlo significance test (Sec. "Monte Carlo Simulations"): totals[s - s_begin] for each
 // shuffle in [s_begin, s_end), the observed total of the unshuffled A, the
 // tally k_ge = #{s : T_s >= T_obs} and p = (k_ge + 1) / (N + 1).
 int or_mc_set(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* clen,
@@ -286,7 +289,8 @@ int or_mc(const uint32_t* a, uint64_t na, const uint32_t* coff, const uint32_t* 
                    k_ge, pvalue, threads);
 }
 
-// Summary of one Monte-Carlo test (Sec. 3.2, Sec. 3.3 and Fig. 3):
+// Summary of one Monte-Carlo test (Sec. "Monte Carlo Simulations", Sec. "Novel
+// genomic relationships" and Fig. 3):
 //   ints[0] observed total        ints[1] k_ge = #{s : T_s >= observed}
 //   ints[2] k_le = #{s : T_s <= observed}
 //   ints[3], ints[4] the two middle totals of the sorted T, at ranks
@@ -329,10 +333,11 @@ int or_mc_summary(const uint64_t* totals, uint64_t n, uint64_t observed, uint64_
   return 0;
 }
 
-// Enumeration problem (Sec. 1.1: report every intersecting pair), by the
-// definition: for each query i in order, every database interval j in index
-// order with b_j meeting a_i.  offsets[i] is the first pair of query i and
-// offsets[na] the number of pairs; pairs (if not NULL) receives (i, j) words.
+// Enumeration problem (Sec. "Interval Set Intersection problem": report every
+// intersecting pair), by the definition: for each query i in order, every
+// database interval j in index order with b_j meeting a_i.  offsets[i] is the
+// first pair of query i and offsets[na] the number of pairs; pairs (if not
+// NULL) receives (i, j) words.
 int or_enumerate_brute(const uint32_t* a, uint64_t na, const uint32_t* b, uint64_t nb,
                        uint64_t* offsets, uint32_t* pairs) {
   if (check_db(b, nb) || check_queries(a, na)) return 1;
@@ -352,7 +357,7 @@ int or_enumerate_brute(const uint32_t* a, uint64_t na, const uint32_t* b, uint64
   return 0;
 }
 
-// Enumeration the way Sec. 2.2 sets it up: B sorted by start (ties in index
+// Enumeration the way Sec. "BITS Algorithm" sets it up: B sorted by start (ties in index
 // order) with each entry's end and index beside it; ICount gives the number
 // c of intervals meeting a, and since every one of them starts before
 // a.end, scanning the entries left of first = #(B_S < a.end) from right to
@@ -399,8 +404,9 @@ int or_enumerate_scan(const uint32_t* a, uint64_t na, const uint32_t* b, uint64_
   return 0;
 }
 
-// Sec. 1.1's predicate exactly as printed, for closed intervals [start, end]:
-// a and b intersect iff a.start <= b.end and a.end >= b.start.  Brute force.
+// The predicate of Sec. "Interval Set Intersection problem" exactly as
+// printed, for closed intervals [start, end]: a and b intersect iff a.start <=
+// b.end and a.end >= b.start.  Brute force.
 int or_count_brute_closed(const uint32_t* a, uint64_t na, const uint32_t* b, uint64_t nb,
                           uint32_t* counts, uint64_t* total) {
   for (uint64_t j = 0; j < nb; ++j)
@@ -422,15 +428,15 @@ int or_count_brute_closed(const uint32_t* a, uint64_t na, const uint32_t* b, uin
   return 0;
 }
 
-// Projection of chromosome-local intervals onto one line (Sec. 2.3): interval
-// i on contig chrom[i] becomes [off[chrom] + start, off[chrom] + end), with one
-// added to the end for closed input, since [s, e] on the integers is
-// [s, e + 1).  With no contig table (nc == 0) every interval is on one
-// contig at offset 0 that spans the whole 32-bit line.  An interval that
-// cannot be projected (contig id out of range, start > end, end past its
-// contig, or an end that does not fit in 32 bits) is written as the inverted
-// pair (2^32 - 1, 0), which every counting call rejects; the return value is
-// the number of such intervals.
+// Projection of chromosome-local intervals onto one line (Sec. "BITS
+// Algorithm" (projection)): interval i on contig chrom[i] becomes [off[chrom]
+// + start, off[chrom] + end), with one added to the end for closed input,
+// since [s, e] on the integers is [s, e + 1).  With no contig table (nc == 0)
+// every interval is on one contig at offset 0 that spans the whole 32-bit
+// line.  An interval that cannot be projected (contig id out of range, start >
+// end, end past its contig, or an end that does not fit in 32 bits) is written
+// as the inverted pair (2^32 - 1, 0), which every counting call rejects; the
+// return value is the number of such intervals.
 uint64_t or_project(const uint32_t* chrom, const uint32_t* start, const uint32_t* end, uint64_t n,
                     const uint32_t* coff, const uint32_t* clen, uint32_t nc, int closed,
                     uint32_t* out) {

@@ -1,12 +1,13 @@
 """Host-side helpers for running BITS across ranks (one GPU per process).
 
-Queries, shuffles and (set, database) pairs are independent (Sec. 2.4
+Queries, shuffles and (set, database) pairs are independent (Sec. "Parallel BITS"
 "pleasingly parallel"), so work shards with no exchange in the data path:
 every rank keeps its own copy of the database and counts its own share.
 The only exchanges are at the end of a call: totals add, and a sharded
 Monte-Carlo test gathers the per-shuffle totals so that every rank can form
-the same tally and p-value (Sec. 3.2).  These helpers work with any
-torch.distributed backend (gloo on CPU, nccl on GPUs).
+the same tally and p-value (Sec. "Monte Carlo Simulations") -- computed by the library's
+bits_mc_summary kernel, never in Python.  The exchange helpers work with
+any torch.distributed backend (gloo on CPU, nccl on GPUs).
 """
 from __future__ import annotations
 
@@ -38,7 +39,9 @@ def combine_totals(local_total: int, group=None) -> int:
 
 
 def gather_shuffle_totals(local_totals: torch.Tensor, n_shuffles: int, group=None) -> torch.Tensor:
-    """All ranks' per-shuffle totals, in shuffle order (ranks hold consecutive ranges)."""
+    """All ranks' per-shuffle totals, in shuffle order (ranks hold consecutive
+    ranges), as int64 words holding the uint64 totals' bits, on the group's
+    device (the GPU for nccl, the host for gloo)."""
     world = dist.get_world_size(group)
     dev = _device(group)
     counts = [shard_bounds(n_shuffles, r, world) for r in range(world)]
@@ -49,13 +52,28 @@ def gather_shuffle_totals(local_totals: torch.Tensor, n_shuffles: int, group=Non
     buf[: loc.numel()] = loc
     parts = [torch.empty_like(buf) for _ in range(world)]
     dist.all_gather(parts, buf, group=group)
-    return torch.cat([p[: hi - lo] for p, (lo, hi) in zip(parts, counts)]).cpu()
+    return torch.cat([p[: hi - lo] for p, (lo, hi) in zip(parts, counts)])
 
 
-def tally(totals: torch.Tensor, observed: int) -> tuple[int, float]:
-    """k_ge = #{s : T_s >= T_obs} and p = (k_ge + 1) / (N + 1) (one IEEE division)."""
-    k = int((totals.to(torch.int64) >= observed).sum().item())
-    return k, (k + 1) / (totals.numel() + 1)
+def sharded_mc(db, a: torch.Tensor, contig_off: torch.Tensor, contig_len: torch.Tensor, *,
+               seed: int, n_shuffles: int, method: int = 0, group=None) -> tuple[torch.Tensor, dict]:
+    """One Monte-Carlo test (Sec. "Monte Carlo Simulations") split over the ranks of `group` by
+    shuffle range: each rank runs bits_mc on its own range of
+    [0, n_shuffles) against its own copy of the database, the ranges'
+    totals are gathered in shuffle order, and bits_mc_summary forms the
+    tally, p-values and Fig. 3 score of the whole run on the GPU.  Returns
+    (all totals as a uint64 CUDA tensor, the summary as a dict).  Needs the
+    nccl backend (the totals stay on the GPU)."""
+    from . import mc_summary
+
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    s0, s1 = shuffle_range(n_shuffles, rank, world)
+    local, observed, _, _ = db.mc(a, contig_off, contig_len, seed=seed, shuffle_begin=s0,
+                                  shuffle_end=s1, method=method)
+    totals = gather_shuffle_totals(local, n_shuffles, group).view(torch.uint64)
+    obs = torch.tensor([observed], dtype=torch.uint64, device=totals.device)
+    stats = mc_summary(totals.view(1, -1), obs).to_dicts()[0]
+    return totals, stats
 
 
 def max_over_ranks(x: float, group=None) -> float:

@@ -27,6 +27,12 @@ def test_reference_arm_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.config_dict(1)          # the same config as the GPU arm's
+    proto = d["protocol"]
+    for k in ("count_all_cores", "count_one_thread", "build_one_thread"):
+        assert proto[k]["runs"] == 5 and proto[k]["mean"] > 0 and proto[k]["sd"] >= 0
 
 
 def test_warmup_below_three_is_rejected():

@@ -1,5 +1,6 @@
-"""Parity of the CUDA enumeration (Sec. 1.1's enumeration problem, the
-count-terminated scan of Sec. 2.2) with the CPU oracle.
+"""Parity of the CUDA enumeration (the enumeration problem of Sec. "Interval
+Set Intersection problem", the count-terminated scan of Sec. "BITS Algorithm")
+with the CPU oracle.
 
 Offsets and pairs must equal the oracle's scan bit for bit, order included
 (descending start, equal starts by descending index), and each query's

@@ -1,5 +1,6 @@
-"""Parity of the Monte-Carlo summary (Sec. 3.2 tallies, Fig. 3 score) and of
-the Monte-Carlo screen over query sets x databases (Sec. 3.3) with the oracle.
+"""Parity of the Monte-Carlo summary (Sec. "Monte Carlo Simulations" tallies,
+Fig. 3 score) and of the Monte-Carlo screen over query sets x databases (Sec.
+"Novel genomic relationships") with the oracle.
 
 Integer fields and p-values must match bit for bit.  The enrichment score is
 log2 of one IEEE division: the division is exact on both sides, and CUDA's

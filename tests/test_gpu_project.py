@@ -1,5 +1,6 @@
-"""Parity of the CUDA projection (Sec. 2.3) and closed-interval mode (Sec. 1.1)
-with the CPU oracle, bit for bit, plus end-to-end closed-interval counts.
+"""Parity of the CUDA projection (Sec. "BITS Algorithm" (projection)) and
+closed-interval mode (Sec. "Interval Set Intersection problem") with the CPU
+oracle, bit for bit, plus end-to-end closed-interval counts.
 """
 import numpy as np
 import pytest

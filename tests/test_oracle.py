@@ -20,7 +20,7 @@ from goldens import (read_count_fixture, read_enumerate_fixture, read_mc_summary
 O = oracle.get()
 
 
-# ------------------------------------------------------------ counting (Sec. 1.1, Alg. 1, Alg. 2)
+# ---------------------------- counting (Sec. "Interval Set Intersection problem", Alg. 1, 2)
 
 @pytest.mark.parametrize("name", ["containment.txt", "duplicates.txt"])
 def test_golden_fixture(name):
@@ -244,7 +244,7 @@ def test_mc_tally_and_pvalue():
     assert (tz == 0).all() and oz == 0 and kz == 9 and pz == 1.0
 
 
-# ------------------------------------------------------- enumeration (Sec. 1.1, Sec. 2.2)
+# ------------------- enumeration (Sec. "Interval Set Intersection problem", "BITS Algorithm")
 
 def _partners(off, pairs, i):
     return [int(x) for x in pairs[int(off[i]):int(off[i + 1]), 1]]
@@ -292,7 +292,7 @@ def test_enumerate_nested_closed_form():
         assert set(_partners(off, pairs, i)) == want
 
 
-# ------------------------------------------- MC summary and per-set streams (Sec. 3.2, 3.3)
+# -- MC summary, per-set streams (Sec. "Monte Carlo Simulations", "Novel genomic relationships")
 
 def _score_ok(got: float, spec: str) -> bool:
     import math
@@ -368,7 +368,7 @@ def test_mc_set_index_streams():
         assert tot[j] == t
 
 
-# ------------------------------------------------ projection and closed intervals (Sec. 1.1, 2.3)
+# ------ projection, closed intervals (Sec. "Interval Set Intersection problem", "BITS Algorithm")
 
 def _expected_rows(rows):
     return np.array([r if r is not None else (0xFFFFFFFF, 0) for r in rows], np.uint32), \

@@ -2,8 +2,8 @@
 
 Every rank counts its slice of the queries (and its range of shuffles) with
 the oracle; the package's host-side helpers combine them.  The combined
-total, the gathered per-shuffle totals and the tally must equal a
-single-process oracle run.  No GPU is used.
+total, the gathered per-shuffle totals and the tally of the gathered
+totals must equal a single-process oracle run.  No GPU is used.
 """
 import os
 import socket
@@ -45,9 +45,11 @@ def _worker(rank, world, port, out):
     s0, s1 = sharding.shuffle_range(97, rank, world, begin=5)
     local, obs, _, _ = o.mc(a, co, cl, bs, be, seed=9, s_begin=s0, s_end=s1)
     gathered = sharding.gather_shuffle_totals(torch.from_numpy(local.astype(np.int64)), 97)
-    k, p = sharding.tally(gathered, obs)
+    # The tally of the gathered totals (bits_mc_summary on a GPU; the
+    # oracle's summary stands in for it on these CPU ranks).
+    st = o.mc_summary(gathered.numpy().view(np.uint64), obs)
     slowest = sharding.max_over_ranks(float(rank + 1))
-    out.put((rank, lo, hi, total, gathered.numpy().tolist(), k, p, slowest))
+    out.put((rank, lo, hi, total, gathered.numpy().tolist(), st["k_ge"], st["p_enrich"], slowest))
     dist.barrier()
     dist.destroy_process_group()
 

@@ -1,6 +1,6 @@
 """Run one named workload a few times, for profiling the library's kernels.
 
-    python -m paper_1208_3407_b300.workloads <name> [--method search|rmi|mergepath] [--reps N]
+    python workloads.py <name> [--method search|rmi|mergepath] [--reps N]
 
 Workloads (inputs from the seeded generator ``bits_synth``):
     count-200k-20m   bits_count, 200,000 queries vs 20,000,000 reads (exome-vs-reads)
@@ -26,12 +26,12 @@ import sys
 import numpy as np
 import torch
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 import bits_synth  # noqa: E402
 
-from . import (METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, Database, count_matrix,  # noqa: E402
-               mc_matrix)
+from paper_1208_3407_b300 import (METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH,  # noqa: E402
+                                  Database, count_matrix, mc_matrix)
 
 METHODS = {"search": METHOD_SEARCH, "rmi": METHOD_RMI, "mergepath": METHOD_MERGEPATH}
 
