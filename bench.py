@@ -6,8 +6,9 @@ against a resident database of 100,000,000 intervals (80 % from a mixture of
 1000 Gaussians, 20 % uniform; lengths log-uniform in [50, 10^4]) with a
 learned index of 2^16 linear leaves per sorted array -- Algorithm 2's
 counting loop over Algorithm 1, per-query uint32 counts plus the uint64
-total.  The headline is the faster of the plain 16-ary search and the
-learned index; both are timed and reported side by side (with merge path).
+total.  The headline is the fastest of the plain 16-ary search, the learned
+index and the autotuned choice (bits_count's AUTO, whose records the line
+also reports); all are timed and reported side by side (with merge path).
 L2 is flushed before every timed step.
 
 Also reported on the same line (most important last, so that a reader of
@@ -66,7 +67,8 @@ SAMPLE_ALL, SAMPLE_ONE, SAMPLE_BUILD, PROTOCOL_RUNS = 1_000_000, 200_000, 10_000
 def config_dict(world: int) -> dict:
     """The headline's config, identical in both arms."""
     return {"workload": HEADLINE,
-            "method": "faster of plain 16-ary search and learned index (both in forms)",
+            "method": "fastest of plain 16-ary search, learned index and the autotuned choice "
+                      "(all in forms)",
             "l2": "flushed (256 MB write) before every timed step; queries 800 MB > L2",
             "parallelism": f"dp{world}: queries and shuffles split across ranks, database "
                            "replicated, no collective in the timed region"}
@@ -278,7 +280,28 @@ def run_reference(args):
 
 # -------------------------------------------------------------------------- our arm
 
+def read_tuning(path: str) -> list:
+    """The autotuner's records of this run (BITS_AUTOTUNE_CACHE lines)."""
+    if not os.path.exists(path):
+        return []
+    out = []
+    for ln in open(path).read().splitlines():
+        f = ln.split()
+        if len(f) >= 6:
+            out.append({"kind": f[1], "log2_queries": int(f[2]), "log2_db": int(f[3]),
+                        "flags": int(f[4]), "values": [int(x) for x in f[5:]]})
+    return out
+
+
 def run_ours(args):
+    # The autotuner records its choices in a fresh file for this run; the
+    # line reports them (kind "count": method, top raise, threads per CTA;
+    # "mc": shuffles and intervals per work unit, top raise; "allpairs":
+    # queries per work unit).
+    tune_path = os.path.join("/tmp", f"bits_autotune_{os.getpid()}.txt")
+    if os.path.exists(tune_path):
+        os.remove(tune_path)
+    os.environ["BITS_AUTOTUNE_CACHE"] = tune_path
     import torch
 
     import bits_synth
@@ -395,8 +418,8 @@ def run_ours(args):
     auto_ms, _, _ = timed(lambda: db4.count(a4, counts=c4, total=t4, check=False), args.steps,
                           args.warmup)
     forms["auto"] = {"ms": auto_ms, "queries_per_s": n4 / (auto_ms * 1e-3)}
-    head = min(("search", "rmi"), key=lambda k: forms[k]["ms"])
-    head_m = bits.METHOD_SEARCH if head == "search" else bits.METHOD_RMI
+    head = min(("search", "rmi", "auto"), key=lambda k: forms[k]["ms"])
+    head_m = {"search": bits.METHOD_SEARCH, "rmi": bits.METHOD_RMI, "auto": bits.METHOD_AUTO}[head]
     head_ms, launches, window = timed(lambda: db4.count(a4, counts=c4, total=t4, method=head_m,
                                                         check=False), args.steps, args.warmup)
     db4.check()
@@ -441,8 +464,13 @@ def run_ours(args):
     rmi_src = ["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/rmi_search.cuh",
                "paper_1208_3407_b300/csrc/rmi.cu"]
     search_src = ["paper_1208_3407_b300/csrc/search.cuh", "paper_1208_3407_b300/csrc/count.cu"]
-    kernel = "k_count_rmi" if head == "rmi" else "k_count_search"
-    src = rmi_src if head == "rmi" else search_src
+    tuned_auto = [r for r in read_tuning(tune_path)
+                  if r["kind"] == "count" and r["flags"] >> 2 == 0 and r["log2_queries"] == 27]
+    head_method = head if head != "auto" else \
+        ({1: "search", 2: "rmi", 3: "mergepath"}.get(tuned_auto[0]["values"][0], "search")
+         if tuned_auto else "search")
+    kernel = "k_count_rmi" if head_method == "rmi" else "k_count_search"
+    src = rmi_src if head_method == "rmi" else search_src
     # DRAM bytes per query from the ncu capture named in profiles/ (valid
     # while the kernel's sources are unchanged), times this rank's queries.
     traffic_q = profiled_value(f"{kernel}_100m", "dram_bytes_per_query", src)
@@ -550,6 +578,7 @@ def run_ours(args):
     line["build_100m_ms"] = sig({"plain": statistics.fmean(t for r, t in build4 if not r),
                                  "with_learned_index": statistics.fmean(t for r, t in build4 if r)})
     line["protocol"] = sig(proto) if proto else None
+    line["tuning"] = read_tuning(tune_path)
     line["forms"] = sig({k: {"ms": v["ms"], "qps": v["queries_per_s"]} for k, v in forms.items()})
     line["mc"] = sig({
         "workload": "100k x 1M, 10,000 shuffles per launch (Table 1 corner)",

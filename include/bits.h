@@ -327,6 +327,47 @@ bits_status bits_sort_intervals_noalloc(const uint32_t* d_b, uint64_t n, uint32_
                                         uint32_t* d_be, void* stream);
 
 /*
+ * Launch parameters (the paper has none of these; none changes a result).
+ * Every call lays out its work with parameters it takes, per field, from
+ * the values pinned on the calling host thread by bits_set_tuning, else from
+ * the autotuner's record for its size class, else from the defaults.  A
+ * size class is (device, ceil log2 of the queries, ceil log2 of the
+ * database, learned index built or not, per-query counts wanted or not, the
+ * method named).  The first bits_count / bits_count_method call of a class
+ * that nothing pins times the candidates on the caller's own inputs with
+ * CUDA events (batches of back-to-back calls, three alternating rounds) and
+ * records the fastest overall (used by BITS_METHOD_AUTO) and the fastest of
+ * each method (used by calls that name their method); bits_mc and
+ * bits_count_matrix time their own candidates the same way on their first
+ * call of a class.  Nothing is timed under stream capture.  When the
+ * environment variable BITS_AUTOTUNE_CACHE names a file, records are read
+ * from it at first use and appended to it as they are made, one line each:
+ *     <device> <kind> <log2 queries> <log2 database> <flags> <values...>
+ * with kind "count" (values: method, top_raise, block), "mc" (mc_shuffles,
+ * mc_chunk, top_raise) or "allpairs" (ap_chunk).
+ */
+typedef struct bits_tuning {
+  int32_t top_raise;    /* plain search in bits_count and bits_mc: levels above the
+                           database's default shared-memory top level to keep in shared
+                           memory instead (0, 1 or 2: a 16x, 256x smaller top, one or two
+                           more tree levels read from memory); -1: tuned */
+  int32_t block;        /* bits_count search kernels: threads per CTA, 256 or 512; 0: tuned */
+  int32_t mc_shuffles;  /* bits_mc: shuffles per work unit (threads per CTA), and */
+  int32_t mc_chunk;     /* intervals per work unit, one of the pairs (256, 1024),
+                           (128, 1024), (256, 512), (256, 2048), (128, 2048); (0, 0): tuned */
+  int32_t ap_chunk;     /* bits_count_matrix: queries per work unit, 4096, 8192, 16384 or
+                           32768; 0: tuned */
+} bits_tuning;
+
+/* Pin launch parameters for later calls on this host thread (NULL: unpin
+ * everything).  BITS_EINVAL, and nothing changes, if a field is outside the
+ * sets listed above. */
+bits_status bits_set_tuning(const bits_tuning* t);
+
+/* The parameters pinned on this host thread (fields at -1 / 0 are tuned). */
+bits_status bits_get_tuning(bits_tuning* t);
+
+/*
  * bits_selftest_wait -- diagnostic of the bounded device-side waits (not in
  * the paper).  Every spin-wait of the library (the radix sort's look-back)
  * gives up after a fixed number of iterations, records a timeout and

@@ -20,6 +20,7 @@ from ._lib import (METHOD_AUTO, METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, Bit
                    LIB_PATH)
 
 __all__ = ["Database", "count_matrix", "project", "mc_summary", "mc_matrix", "McStats",
+           "set_tuning", "get_tuning", "tuning",
            "kernel_launches", "BitsError", "METHOD_AUTO",
            "METHOD_SEARCH", "METHOD_RMI", "METHOD_MERGEPATH", "LIB_PATH", "device_view"]
 
@@ -400,6 +401,37 @@ def mc_matrix(dbs, a_sets, contig_off: torch.Tensor, contig_len: torch.Tensor, *
                             _stream_ptr(stream))
     _lib.check(st, "bits_mc_matrix")
     return observed, totals, (McStats(raw) if raw is not None else None)
+
+
+def set_tuning(top_raise: int = -1, block: int = 0, mc_shuffles: int = 0, mc_chunk: int = 0,
+               ap_chunk: int = 0) -> None:
+    """Pin launch parameters for later calls on this thread (bits_set_tuning);
+    the defaults unpin (the autotuner decides)."""
+    t = _lib.Tuning(top_raise, block, mc_shuffles, mc_chunk, ap_chunk)
+    _lib.check(_lib.load().bits_set_tuning(C.byref(t)), "bits_set_tuning")
+
+
+def get_tuning() -> dict:
+    """The parameters pinned on this thread (-1 / 0: tuned)."""
+    t = _lib.Tuning()
+    _lib.check(_lib.load().bits_get_tuning(C.byref(t)), "bits_get_tuning")
+    return {f: getattr(t, f) for f, _ in _lib.Tuning._fields_}
+
+
+class tuning:
+    """Context manager: pin launch parameters inside a ``with`` block."""
+
+    def __init__(self, **kw):
+        self.kw = kw
+
+    def __enter__(self):
+        self.prev = get_tuning()
+        set_tuning(**self.kw)
+        return self
+
+    def __exit__(self, *exc):
+        set_tuning(**self.prev)
+        return False
 
 
 def kernel_launches() -> int:

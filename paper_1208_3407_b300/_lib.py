@@ -22,7 +22,8 @@ METHOD_AUTO, METHOD_SEARCH, METHOD_RMI, METHOD_MERGEPATH = range(4)
 EXPORTS = ["bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc",
            "bits_count_matrix", "bits_db_info", "bits_check", "bits_free", "bits_last_error", "bits_kernel_launches",
            "bits_sort_intervals_noalloc", "bits_db_rmi", "bits_selftest_wait", "bits_project",
-           "bits_mc_summary", "bits_mc_matrix", "bits_enumerate_offsets", "bits_enumerate_pairs"]
+           "bits_mc_summary", "bits_mc_matrix", "bits_enumerate_offsets", "bits_enumerate_pairs",
+           "bits_set_tuning", "bits_get_tuning"]
 
 
 class BitsError(RuntimeError):
@@ -37,6 +38,11 @@ class Opts(C.Structure):
 
 
 FLAG_ENUMERATE = 1
+
+
+class Tuning(C.Structure):
+    _fields_ = [("top_raise", C.c_int32), ("block", C.c_int32), ("mc_shuffles", C.c_int32),
+                ("mc_chunk", C.c_int32), ("ap_chunk", C.c_int32)]
 
 
 _lib = None
@@ -66,6 +72,8 @@ def load():
     lib.bits_check.argtypes = [vp, vp]
     lib.bits_sort_intervals_noalloc.argtypes = [u32p, C.c_uint64, u32p, u32p, vp]
     lib.bits_selftest_wait.argtypes = [C.c_uint32, vp]
+    lib.bits_set_tuning.argtypes = [C.POINTER(Tuning)]
+    lib.bits_get_tuning.argtypes = [C.POINTER(Tuning)]
     lib.bits_enumerate_offsets.argtypes = [vp, u32p, C.c_uint64, u64p, vp]
     lib.bits_enumerate_pairs.argtypes = [vp, u32p, C.c_uint64, u64p, u32p, vp]
     lib.bits_mc_summary.argtypes = [u64p, C.c_uint32, C.c_uint32, u64p, vp, vp]
@@ -79,7 +87,8 @@ def load():
     for f in ("bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc",
               "bits_count_matrix", "bits_db_info", "bits_check", "bits_sort_intervals_noalloc", "bits_db_rmi",
               "bits_selftest_wait", "bits_project", "bits_mc_summary", "bits_mc_matrix",
-              "bits_enumerate_offsets", "bits_enumerate_pairs"):
+              "bits_enumerate_offsets", "bits_enumerate_pairs", "bits_set_tuning",
+              "bits_get_tuning"):
         getattr(lib, f).restype = st
     lib.bits_free.argtypes = [vp]
     lib.bits_free.restype = None

@@ -3,7 +3,9 @@
 // persistent launch.
 //
 // Work is split by query count: a unit is (database j, query set i, chunk of
-// kChunk queries), and units are listed database by database, largest
+// up to C queries; C = 8192 by default, tuned per argument shape among 4096
+// .. 32768 by timing the launch once per candidate on the first call), and
+// units are listed database by database, largest
 // database first, so the deepest (slowest) searches start early and the
 // small units fill the tail.  CTAs take units from an atomic ticket; a CTA
 // reloads its shared-memory top level only when its unit's database differs
@@ -25,12 +27,12 @@
 #include "rmi.cuh"
 #include "rmi_search.cuh"
 #include "search.cuh"
+#include "tune.cuh"
 
 namespace bits {
 namespace {
 
 constexpr int kApBlock = 256;
-constexpr uint32_t kChunk = 8192;
 
 struct MatDb {
   LevelIndex L;
@@ -137,7 +139,7 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
                              uint64_t* d_matrix, cudaStream_t st) {
   if (n_db == 0 || n_sets == 0) return BITS_OK;
   std::vector<uint64_t> key;
-  key.push_back(reinterpret_cast<uintptr_t>(d_matrix));
+  key.push_back(reinterpret_cast<uintptr_t>(d_matrix) ^ ((uint64_t)pinned_tuning().ap_chunk << 48));
   for (uint32_t j = 0; j < n_db; ++j) key.push_back(reinterpret_cast<uintptr_t>(dbs[j]));
   for (uint32_t i = 0; i < n_sets; ++i) {
     key.push_back(reinterpret_cast<uintptr_t>(d_as[i]));
@@ -161,11 +163,14 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
     for (uint32_t j = 0; j < n_db; ++j) {
       int m = BITS_METHOD_SEARCH;
       if (dbs[j]->has_rmi && n_sample) {
-        bits_status s = autotune_count(dbs[j], d_as[big], n_sample, nullptr, d_tmp, st, &m);
+        TuneCount t;
+        bits_status s = autotune_count(dbs[j], d_as[big], n_sample, nullptr, d_tmp, st,
+                                       BITS_METHOD_AUTO, &t);
         if (s != BITS_OK) {
           pool_free(d_tmp, st);
           return s;
         }
+        m = t.method;
       }
       hd[j].L = dbs[j]->lvl;
       hd[j].R = dbs[j]->has_rmi ? rmi_view(dbs[j]) : RmiView{};
@@ -175,41 +180,96 @@ bits_status run_count_matrix(const bits_db* const* dbs, uint32_t n_db,
       if (m != BITS_METHOD_RMI) max_top = std::max<size_t>(max_top, top_words(dbs[j]->lvl.top_size));
     }
     pool_free(d_tmp, st);
-    // Units: largest database first, then set by set, kChunk queries each.
+    // Units: largest database first, then set by set, `chunk` queries each.
     std::vector<uint32_t> order(n_db);
     for (uint32_t j = 0; j < n_db; ++j) order[j] = j;
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t x, uint32_t y) { return dbs[x]->n > dbs[y]->n; });
-    std::vector<MatUnit> units;
-    for (uint32_t j : order)
-      for (uint32_t i = 0; i < n_sets; ++i)
-        for (uint64_t s0 = 0; s0 < n_as[i]; s0 += kChunk)
-          units.push_back(MatUnit{j, i, (uint32_t)s0,
-                                  (uint32_t)std::min<uint64_t>(kChunk, n_as[i] - s0)});
+    auto make_units = [&](uint32_t chunk) {
+      std::vector<MatUnit> units;
+      for (uint32_t j : order)
+        for (uint32_t i = 0; i < n_sets; ++i)
+          for (uint64_t s0 = 0; s0 < n_as[i]; s0 += chunk)
+            units.push_back(MatUnit{j, i, (uint32_t)s0,
+                                    (uint32_t)std::min<uint64_t>(chunk, n_as[i] - s0)});
+      return units;
+    };
+    uint64_t total_q = 0, total_db = 0;
+    for (uint32_t i = 0; i < n_sets; ++i) total_q += n_as[i];
+    for (uint32_t j = 0; j < n_db; ++j) total_db += dbs[j]->n;
+    bool tuned = false;
+    uint32_t chunk = (uint32_t)ap_chunk_params(total_q, total_db, n_db, n_sets, &tuned);
+    // Room for the unit list of the smallest candidate chunk.
+    const size_t max_units = std::max<size_t>(make_units(kApChunks[0]).size(), 1);
     g = std::make_shared<MatGraph>();
     const size_t off_units = align256(sizeof(MatDb) * n_db);
-    const size_t off_sets = off_units + align256(sizeof(MatUnit) * std::max<size_t>(units.size(), 1));
+    const size_t off_sets = off_units + align256(sizeof(MatUnit) * max_units);
     const size_t off_ticket = off_sets + align256(sizeof(void*) * n_sets);
     BITS_CUDA_TRY(cudaMalloc(&g->dev, off_ticket + 256));
     char* base = static_cast<char*>(g->dev);
     std::vector<const void*> sets(d_as, d_as + n_sets);
     BITS_CUDA_TRY(cudaMemcpy(base, hd.data(), sizeof(MatDb) * n_db, cudaMemcpyHostToDevice));
-    if (!units.empty())
-      BITS_CUDA_TRY(cudaMemcpy(base + off_units, units.data(), sizeof(MatUnit) * units.size(),
-                               cudaMemcpyHostToDevice));
     BITS_CUDA_TRY(cudaMemcpy(base + off_sets, sets.data(), sizeof(void*) * n_sets,
                              cudaMemcpyHostToDevice));
     MatArgs P{};
     P.dbs = reinterpret_cast<const MatDb*>(base);
     P.units = reinterpret_cast<const MatUnit*>(base + off_units);
-    P.n_units = (uint32_t)units.size();
     P.sets = reinterpret_cast<const uint2* const*>(base + off_sets);
     P.matrix = reinterpret_cast<unsigned long long*>(d_matrix);
     P.n_db = n_db;
     P.ticket = reinterpret_cast<uint32_t*>(base + off_ticket);
     const size_t smem = sizeof(uint32_t) * 2 * max_top;
-    const uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(P.n_units, 1),
-                                             (uint32_t)(ap_blocks_per_sm(smem) * sm_count()));
+    const uint32_t per_sm_grid = (uint32_t)(ap_blocks_per_sm(smem) * sm_count());
+    auto upload = [&](uint32_t c) -> bits_status {
+      const std::vector<MatUnit> units = make_units(c);
+      if (!units.empty())
+        BITS_CUDA_TRY(cudaMemcpy(base + off_units, units.data(), sizeof(MatUnit) * units.size(),
+                                 cudaMemcpyHostToDevice));
+      P.n_units = (uint32_t)units.size();
+      return BITS_OK;
+    };
+    if (!tuned && !stream_capturing(st)) {
+      // Time one launch per candidate chunk (after a warm-up launch of each)
+      // and record the fastest for this argument shape.
+      cudaEvent_t e0, e1;
+      BITS_CUDA_TRY(cudaEventCreate(&e0));
+      BITS_CUDA_TRY(cudaEventCreate(&e1));
+      float best = 1e30f;
+      uint32_t best_c = chunk;
+      bits_status s = BITS_OK;
+      for (int round = 0; round < 2 && s == BITS_OK; ++round)
+        for (int c : kApChunks) {
+          s = upload((uint32_t)c);
+          if (s != BITS_OK) break;
+          const uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(P.n_units, 1), per_sm_grid);
+          cudaMemsetAsync(d_matrix, 0, sizeof(uint64_t) * (size_t)n_sets * n_db, st);
+          cudaMemsetAsync(P.ticket, 0, sizeof(uint32_t), st);
+          cudaEventRecord(e0, st);
+          k_allpairs<<<grid, kApBlock, smem, st>>>(P);
+          count_launch();
+          cudaEventRecord(e1, st);
+          float ms = 0.f;
+          if (cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            s = cuda_status(cudaGetLastError(), "count_matrix tuning");
+            break;
+          }
+          if (round > 0 && ms < best) {
+            best = ms;
+            best_c = (uint32_t)c;
+          }
+        }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (s != BITS_OK) return s;
+      chunk = best_c;
+      ap_chunk_record(total_q, total_db, n_db, n_sets, (int)chunk);
+    }
+    {
+      const bits_status s = upload(chunk);
+      if (s != BITS_OK) return s;
+    }
+    const uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(P.n_units, 1), per_sm_grid);
 
     cudaStream_t cap = nullptr;
     BITS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));

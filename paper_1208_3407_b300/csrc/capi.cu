@@ -49,41 +49,50 @@ int sm_count() {
   return g_sm_count[dev];
 }
 
-int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap) {
-  int dev = 0, per_sm_smem = 0, reserved = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, smem);
-  b = std::max(1, std::min(b, cap));
-  if (per_sm_smem > 0) {
-    const double need = (double)b * (double)(smem + (size_t)reserved);
-    const int pct = std::min(100, (int)std::ceil(100.0 * need / per_sm_smem));
-    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  }
-  return b;
-}
-
 int kernel_blocks_per_sm(const void* kernel, int block, size_t smem, int cap) {
+  // Per (device, kernel): the largest dynamic shared-memory limit set so far
+  // (the limit only grows, so every earlier launch size stays valid), the
+  // shared-memory size the carveout was last fitted to, and the occupancy
+  // per (block, smem, cap).
+  struct State {
+    size_t limit = 0;
+    size_t carve_for = ~size_t(0);
+    std::map<std::tuple<int, size_t, int>, int> occ;
+  };
   static std::mutex mu;
-  static std::map<std::tuple<int, const void*, int, size_t, int>, int> cache;
+  static std::map<std::pair<int, const void*>, State> states;
   int dev = 0;
   cudaGetDevice(&dev);
-  const auto key = std::make_tuple(dev, kernel, block, smem, cap);
   std::lock_guard<std::mutex> lk(mu);
-  auto it = cache.find(key);
-  if (it != cache.end()) return it->second;
-  int b = 0;
-  if (cap > 0) {
-    b = occupancy_with_l1(kernel, block, smem, cap);
-  } else {
+  State& S = states[std::make_pair(dev, kernel)];
+  if (smem > S.limit) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    S.limit = smem;
+  }
+  const auto key = std::make_tuple(block, smem, cap);
+  auto it = S.occ.find(key);
+  int b = 0;
+  if (it != S.occ.end()) {
+    b = it->second;
+  } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, smem);
     b = std::max(1, b);
+    if (cap > 0) b = std::min(b, cap);
+    S.occ.emplace(key, b);
   }
-  cache.emplace(key, b);
+  if (cap > 0 && S.carve_for != smem) {
+    // Fit the shared-memory carveout to b CTAs so the rest of the SM's
+    // on-chip memory stays L1.
+    int per_sm_smem = 0, reserved = 0;
+    cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (per_sm_smem > 0) {
+      const double need = (double)b * (double)(smem + (size_t)reserved);
+      const int pct = std::min(100, (int)std::ceil(100.0 * need / per_sm_smem));
+      cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    }
+    S.carve_for = smem;
+  }
   return b;
 }
 
@@ -196,7 +205,7 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   const size_t off_be = align_up(off_bs + sizeof(uint32_t) * n16, 256);
   const size_t off_lv = align_up(off_be + sizeof(uint32_t) * n16, 256);
   const size_t off_top = align_up(off_lv + sizeof(uint32_t) * db->plan.level_words, 256);
-  const size_t off_err = align_up(off_top + sizeof(uint32_t) * 2 * db->plan.top_size, 256);
+  const size_t off_err = align_up(off_top + sizeof(uint32_t) * db->plan.top_words, 256);
   const size_t off_rmi = align_up(off_err + 256, 256);
   const size_t leaves = db->has_rmi ? (1ull << o.rmi_leaves_log2) : 0;
   const size_t off_enum = align_up(off_rmi + 2 * leaves * sizeof(bits_rmi_leaf), 256);
@@ -303,26 +312,22 @@ bits_status bits_count_method(const bits_db* db, int32_t method, const uint32_t*
     set_error("bits_count: misaligned pointer (queries 8 B, counts 4 B, total 8 B)");
     return BITS_EINVAL;
   }
+  if (method < BITS_METHOD_AUTO || method > BITS_METHOD_MERGEPATH) {
+    set_error("bits_count: unknown method");
+    return BITS_EINVAL;
+  }
+  if (method == BITS_METHOD_RMI && !db->has_rmi) {
+    set_error("bits_count: database was built without a learned index");
+    return BITS_ENOTIMPL;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (method == BITS_METHOD_AUTO) {
-    bits_status s = autotune_count(db, d_a, (uint32_t)n, d_counts, d_total, st, &method);
-    if (s != BITS_OK) return s;
-  }
-  switch (method) {
-    case BITS_METHOD_SEARCH:
-      return launch_count_search(db, d_a, (uint32_t)n, d_counts, d_total, st);
-    case BITS_METHOD_RMI:
-      if (!db->has_rmi) {
-        set_error("bits_count: database was built without a learned index");
-        return BITS_ENOTIMPL;
-      }
-      return launch_count_rmi(db, d_a, (uint32_t)n, d_counts, d_total, st);
-    case BITS_METHOD_MERGEPATH:
-      return launch_count_mergepath(db, d_a, (uint32_t)n, d_counts, d_total, st);
-    default:
-      set_error("bits_count: unknown method");
-      return BITS_EINVAL;
-  }
+  // Method (for AUTO), shared-memory top and CTA size: pinned, tuned for
+  // this size class (timed here the first time the class is seen), or the
+  // defaults.
+  TuneCount t;
+  bits_status s = autotune_count(db, d_a, (uint32_t)n, d_counts, d_total, st, method, &t);
+  if (s != BITS_OK) return s;
+  return launch_count_tuned(db, t, d_a, (uint32_t)n, d_counts, d_total, st);
 }
 
 bits_status bits_count(const bits_db* db, const uint32_t* d_a, uint64_t n, uint32_t* d_counts,

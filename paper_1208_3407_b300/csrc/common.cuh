@@ -29,17 +29,13 @@ void set_error(const std::string& msg);
 void count_launch(uint32_t k = 1);
 void uncount_launch(uint64_t k);
 int sm_count();
-// Resident CTAs per SM for a kernel with `smem` bytes of dynamic shared
-// memory, capped at `cap`, with the shared-memory carveout set to what that
-// many CTAs need so the rest of the SM's on-chip memory stays L1 (defined in
-// capi.cu).
-int occupancy_with_l1(const void* kernel, int block, size_t smem, int cap);
 // Resident CTAs per SM of `kernel` with `block` threads and `smem` bytes of
-// dynamic shared memory on the current device (at least 1), after raising
-// the kernel's dynamic shared-memory limit to `smem` on that device.  Both
-// are per-device settings, so the result is cached per (device, kernel,
-// block, smem) under a lock; with cap > 0 it goes through
-// occupancy_with_l1 (carveout fitted to `cap` CTAs).
+// dynamic shared memory on the current device (at least 1; at most `cap`
+// when cap > 0).  The kernel's dynamic shared-memory limit on the device is
+// raised to `smem` if it is lower (it never drops, so earlier launch sizes
+// stay valid); with cap > 0 the shared-memory carveout is fitted to that
+// many CTAs so the rest of the SM's on-chip memory stays L1.  Both are
+// per-device settings, kept per (device, kernel) under a lock.
 int kernel_blocks_per_sm(const void* kernel, int block, size_t smem, int cap = 0);
 bits_status cuda_status(cudaError_t e, const char* what);
 // Device memory from the library's stream-ordered pool, one per device,

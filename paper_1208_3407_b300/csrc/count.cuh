@@ -3,6 +3,7 @@
 
 #include "common.cuh"
 #include "db.cuh"
+#include "tune.cuh"
 
 namespace bits {
 
@@ -24,16 +25,14 @@ bits_status launch_zero_total(uint64_t* d_total, cudaStream_t st);
 // Plain BITS count through the 16-ary levels.  Zeroes *d_total (a one-CTA
 // kernel the count kernel overlaps as a programmatic dependent), then
 // accumulates; d_counts may be NULL.
+// tc: the tuned parameters (raise, block) to use; NULL takes them from
+// count_params (pinned, tuned or default).
 bits_status launch_count_search(const bits_db* db, const uint32_t* d_a, uint32_t n,
-                                uint32_t* d_counts, uint64_t* d_total, cudaStream_t st);
+                                uint32_t* d_counts, uint64_t* d_total, cudaStream_t st,
+                                const TuneCount* tc = nullptr);
 
-// Method already chosen for an AUTO count of n queries (the untuned default
-// when the size class has not been timed yet).
-int choose_count_method(const bits_db* db, uint32_t n);
-
-// Method for an AUTO count: times the built methods on these inputs the first
-// time a size class is seen (the outputs are overwritten by the final run).
-bits_status autotune_count(const bits_db* db, const uint32_t* d_a, uint32_t n,
-                           uint32_t* d_counts, uint64_t* d_total, cudaStream_t st, int* method);
+// A view of the database's levels whose shared-memory top is `raise` levels
+// above the default one (clamped to the levels kept), for the search kernels.
+LevelIndex level_view(const bits_db* db, int raise);
 
 }  // namespace bits

@@ -52,21 +52,6 @@ bits_status device_alias(const void* p, size_t bytes, const void** dev, const ch
   return BITS_OK;
 }
 
-bits_status dispatch(const bits_db* db, int method, const uint32_t* d_a, uint32_t n,
-                     uint32_t* d_counts, uint64_t* d_total, cudaStream_t st) {
-  switch (method) {
-    case BITS_METHOD_SEARCH:
-      return launch_count_search(db, d_a, n, d_counts, d_total, st);
-    case BITS_METHOD_RMI:
-      return launch_count_rmi(db, d_a, n, d_counts, d_total, st);
-    case BITS_METHOD_MERGEPATH:
-      return launch_count_mergepath(db, d_a, n, d_counts, d_total, st);
-    default:
-      set_error("bits_count_host: unknown method");
-      return BITS_EINVAL;
-  }
-}
-
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
@@ -94,11 +79,14 @@ extern "C" bits_status bits_count_host(const bits_db* db, int32_t method, const 
     set_error("bits_count_host: unknown method");
     return BITS_EINVAL;
   }
-  if (method == BITS_METHOD_AUTO) method = choose_count_method(db, (uint32_t)n);
   if (method == BITS_METHOD_RMI && !db->has_rmi) {
     set_error("bits_count_host: database was built without a learned index");
     return BITS_ENOTIMPL;
   }
+  // Method (for AUTO), top and CTA size as recorded for this size class (the
+  // host-buffer path itself never times candidates).
+  const TuneCount tuned = count_params(db, method, (uint32_t)n, h_counts != nullptr);
+  method = tuned.method;
   int cur = 0;
   BITS_CUDA_TRY(cudaGetDevice(&cur));
   if (cur != db->device) {
@@ -144,7 +132,7 @@ extern "C" bits_status bits_count_host(const bits_db* db, int32_t method, const 
   }
   if (stage_c) d_c = reinterpret_cast<uint32_t*>(buf + off_c);
 
-  s = dispatch(db, method, d_a, (uint32_t)n, d_c, d_total, st);
+  s = launch_count_tuned(db, tuned, d_a, (uint32_t)n, d_c, d_total, st);
   if (s != BITS_OK) return done(s);
   if (stage_c) {
     cudaError_t e = cudaMemcpyAsync(h_counts, d_c, c_bytes, cudaMemcpyDeviceToHost, st);

@@ -35,13 +35,21 @@ struct bits_rmi {
 
 struct bits_mc_graph;  // cached CUDA graph of one bits_mc argument set (mc.cu)
 
-// Sizes of the implicit 16-ary tree (see search.cuh).
+// Sizes of the implicit 16-ary tree (see search.cuh).  The default top
+// level J is the largest that fits the shared-memory cap; levels J+1 ..
+// Tmax (each 16 times smaller) are also kept, with a top image each, so a
+// launch may search a smaller top in shared memory and read the levels
+// below it from memory instead (a tuning choice, same counts).
 struct LevelPlan {
-  int J = 0;                           // top level, kept in shared memory
+  int J = 0;                           // default top level
+  int Tmax = 0;                        // highest level a launch may use as its top
   uint32_t len[bits::kMaxLevels + 1] = {};
-  size_t off[bits::kMaxLevels] = {};   // word offset of level j (0 <= j < J) in the level storage
-  size_t level_words = 0;              // words of levels 0 .. J-1, both arrays interleaved
-  uint32_t top_size = 4;               // shared-memory entries per array (power of two)
+  size_t off[bits::kMaxLevels] = {};   // word offset of level j (0 <= j < Tmax) in the level storage
+  size_t level_words = 0;              // words of levels 0 .. Tmax-1, both arrays interleaved
+  uint32_t top_size = 4;               // entries per array of the default top image
+  uint32_t top_size_at[bits::kMaxLevels + 1] = {};  // image size of top level t (J <= t <= Tmax)
+  size_t top_off[bits::kMaxLevels + 1] = {};        // word offset of that image ([2][size])
+  size_t top_words = 0;                // words of all top images
 };
 
 struct bits_db {
@@ -50,7 +58,7 @@ struct bits_db {
   uint32_t* bs = nullptr;      // sorted starts, padded with 0xFFFFFFFF to 16 (device)
   uint32_t* be = nullptr;      // sorted ends, padded the same way (device)
   uint32_t* levels = nullptr;  // levels 0 .. J-1 of both arrays, interleaved by node (device)
-  uint32_t* top = nullptr;     // top-level images [2][top_size] (device)
+  uint32_t* top = nullptr;     // top-level images, [2][top_size_at[t]] for J <= t <= Tmax (device)
   LevelPlan plan;
   bits::LevelIndex lvl{};      // kernel-side view of the levels
   uint32_t* err = nullptr;   // device error word (DEV_ERR_* bits)
@@ -61,9 +69,10 @@ struct bits_db {
   void* block = nullptr;     // the one device allocation owning all of the above
   size_t block_bytes = 0;
   // Cached MC graphs keyed by the call's arguments (method, queries, n,
-  // contig table, seed, shuffle range, totals), at most 16.
+  // contig table, seed, shuffle range, totals) and its launch parameters,
+  // at most 16.
   using McKey = std::tuple<int, const void*, uint64_t, const void*, const void*, uint32_t, uint64_t,
-                           uint32_t, uint32_t, void*>;
+                           uint32_t, uint32_t, void*, int>;
   bits::GraphCache<McKey, bits_mc_graph> mc_graphs{16};
 };
 

@@ -17,8 +17,8 @@
 
 namespace bits {
 
-constexpr int kMcBlock = 256;    // shuffles per work unit (one per thread)
-constexpr int kMcChunk = 1024;   // intervals per work unit
+constexpr int kMcBlock = 256;    // default shuffles per work unit (one per thread)
+constexpr int kMcChunk = 1024;   // default intervals per work unit
 constexpr int kMaxContigs = 4096;
 static_assert(kMcChunk % kMcBlock == 0, "a chunk is staged in whole rounds of the block");
 // Resident CTAs per SM of the Monte-Carlo kernels: the shared-memory top and
@@ -47,22 +47,24 @@ __device__ __forceinline__ int contig_of(const uint32_t* s_coff, uint32_t nc, ui
 // inverted, lies before the first contig or crosses its contig's end sets
 // `bad` and is pinned in place (range 1, length 0).  Each thread issues all
 // of its loads before it uses any, so a chunk costs one memory round trip.
-// Must be called by exactly kMcBlock threads.
+// Must be called by exactly BLOCK threads; CHUNK is a multiple of BLOCK.
+template <int BLOCK = kMcBlock, int CHUNK = kMcChunk>
 __device__ __forceinline__ void mc_stage_chunk(const uint2* __restrict__ A, uint32_t i0,
                                                uint32_t cn, const uint32_t* s_coff,
                                                const uint32_t* s_clen, uint32_t nc,
                                                uint32_t* s_off, uint32_t* s_len, uint32_t* s_rng,
                                                bool& bad) {
-  constexpr int kPer = kMcChunk / kMcBlock;
+  static_assert(CHUNK % BLOCK == 0, "a chunk is staged in whole rounds of the block");
+  constexpr int kPer = CHUNK / BLOCK;
   uint2 qs[kPer];
   #pragma unroll
   for (int r = 0; r < kPer; ++r) {
-    const uint32_t k = threadIdx.x + (uint32_t)r * kMcBlock;
+    const uint32_t k = threadIdx.x + (uint32_t)r * BLOCK;
     qs[r] = k < cn ? A[i0 + k] : make_uint2(0u, 0u);
   }
   #pragma unroll
   for (int r = 0; r < kPer; ++r) {
-    const uint32_t k = threadIdx.x + (uint32_t)r * kMcBlock;
+    const uint32_t k = threadIdx.x + (uint32_t)r * BLOCK;
     if (k >= cn) continue;
     const uint2 q = qs[r];
     const int c = contig_of(s_coff, nc, q.x);
@@ -94,11 +96,12 @@ struct McLane {
   bool active;
 };
 
+template <int BLOCK = kMcBlock>
 __device__ __forceinline__ McLane mc_lane(uint32_t sb, uint32_t n_shuffles) {
-  const uint32_t first = sb * kMcBlock;
-  const uint32_t ns = min((uint32_t)kMcBlock, n_shuffles - first);
+  const uint32_t first = sb * BLOCK;
+  const uint32_t ns = min((uint32_t)BLOCK, n_shuffles - first);
   McLane l;
-  l.groups = kMcBlock / ns;
+  l.groups = BLOCK / ns;
   l.group = threadIdx.x / ns;
   l.s_local = first + threadIdx.x % ns;
   l.active = l.group < l.groups;

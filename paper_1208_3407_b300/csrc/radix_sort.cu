@@ -1,5 +1,7 @@
-// LSD radix sort of interval starts and ends (Algorithm 2's two Sort steps;
-// Sec. "Parallel BITS" relies on a GPU radix sort for them), keys only or key/value.
+// LSD radix sort of key/value pairs drawn from interval pairs: the
+// enumeration database's start order with interval indices and the merge
+// path's query sort (Algorithm 2's Sort steps with values; the keys-only
+// database sort of Sec. "Parallel BITS" is sort_keys.cu).
 //
 // Design (one GPU, HBM-bound):
 //   * k_radix_hist reads the interval array once, validates it, and builds
@@ -8,17 +10,15 @@
 //     the first pass derives them).
 //   * k_onesweep runs one digit pass for both key arrays in one launch.  A
 //     tile of 8192 keys is ranked stably inside the CTA (bit-sliced ballots
-//     and per-warp shared-memory counters), its per-digit counts are published to a decoupled look-back
-//     table, and the CTA gathers the exclusive prefix of earlier tiles from
-//     that table: one thread per digit reads eight predecessor tiles per
-//     round trip and stops at the nearest tile that has published its
-//     inclusive prefix.  Keys (and values) are staged in digit order in
-//     shared memory so that stores of one digit are contiguous.  The first
-//     pass reads its key straight out of the interval array, so there is no
-//     separate split step; in key/value mode the first pass's value is the
-//     interval's index (top bit set if the interval is inverted).  Tiles
-//     take ticket numbers in launch order, so a tile only waits on tiles
-//     that already run; every wait is bounded and reports DEV_ERR_TIMEOUT.
+//     and per-warp shared-memory counters), its per-digit counts are
+//     published to a decoupled look-back table, and the CTA gathers the
+//     exclusive prefix of earlier tiles from that table (sort_common.cuh).
+//     Keys and values are staged in digit order in shared memory so that
+//     stores of one digit are contiguous.  The first pass reads its key
+//     straight out of the interval array; its value is the interval's index
+//     (top bit set if the interval is inverted).  Tiles take ticket numbers
+//     in launch order, so a tile only waits on tiles that already run; every
+//     wait is bounded and reports DEV_ERR_TIMEOUT.
 //   * Passes whose digit is the same for every key are skipped (the host
 //     reads the histograms once, together with the validation flag).
 //
@@ -27,21 +27,18 @@
 // doubled for values.
 #include "common.cuh"
 #include "radix_sort.cuh"
+#include "sort_common.cuh"
 
 namespace bits {
 namespace {
 
-constexpr int kRadix = 256;
-constexpr int kPasses = 4;
 constexpr int kHistBlock = 512;
 constexpr int kSwBlock = 512;
 constexpr int kSwWarps = kSwBlock / 32;
 constexpr int kSwKpt = 16;
 constexpr int kSwTile = kSwBlock * kSwKpt;  // 8192 keys
 static_assert(kSwTile == (int)kRadixTileKeys, "tile size shared with the look-back sizing");
-constexpr int kLookAhead = 8;  // predecessor status words read per round trip
 constexpr int kCnt = kRadix + 1;  // per-warp counters: 256 digits + the tail's empty lanes
-constexpr uint32_t kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kValMask = (1u << 30) - 1;
 
 // validate: 0 = database (end > start required, else DEV_ERR_INVALID),
 //           1 = queries (end < start sets *inv, not an error here).
@@ -88,33 +85,6 @@ struct SweepJob {
 struct SweepJobs {
   SweepJob j[2];
 };
-
-// Exclusive scan of one value per thread over threads [0, 256); every
-// thread of the block must call it.
-__device__ __forceinline__ uint32_t scan256_excl(uint32_t v, uint32_t* s_w) {
-  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
-  uint32_t x = threadIdx.x < kRadix ? v : 0u;
-  #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-    if (lane >= (unsigned)o) x += y;
-  }
-  if (threadIdx.x < kRadix && lane == 31) s_w[w] = x;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint32_t t = lane < kRadix / 32 ? s_w[lane] : 0u;
-    #pragma unroll
-    for (int o = 1; o < kRadix / 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
-      if (lane >= (unsigned)o) t += y;
-    }
-    if (lane < kRadix / 32) s_w[lane] = t;
-  }
-  __syncthreads();
-  const uint32_t r = (threadIdx.x < kRadix) ? (x - v + (w > 0 ? s_w[w - 1] : 0u)) : 0u;
-  __syncthreads();
-  return r;
-}
 
 template <bool KV>
 __global__ void __launch_bounds__(kSwBlock, 2)
@@ -260,43 +230,9 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
     }
   }
 
-  // Decoupled look-back, one thread per digit, eight predecessors per round
-  // trip: their status words are loaded together, then consumed nearest
-  // first until a tile with its inclusive prefix is reached.
+  // Decoupled look-back (sort_common.cuh), one thread per digit.
   if (tile > 0 && tid < kRadix) {
-    uint32_t excl = 0u, spins = 0u;
-    int hi = (int)tile;  // next predecessor to consume is hi - 1
-    bool done = false;
-    while (!done) {
-      uint32_t v[kLookAhead];
-      #pragma unroll
-      for (int k = 0; k < kLookAhead; ++k) {
-        const int t = hi - 1 - k;
-        v[k] = t >= 0 ? *(volatile const uint32_t*)(status + (size_t)t * kRadix + tid) : kFlagPre;
-      }
-      int used = 0;
-      bool stalled = false;
-      #pragma unroll
-      for (int k = 0; k < kLookAhead; ++k) {
-        if (done || stalled) continue;
-        const uint32_t fl = v[k] & ~kValMask;
-        if (fl == 0u) {
-          stalled = true;
-          continue;
-        }
-        excl += v[k] & kValMask;
-        ++used;
-        if (fl == kFlagPre) done = true;
-      }
-      hi -= used;
-      if (!done && stalled) {
-        if (++spins > kSpinLimit) {
-          set_dev_error(err, DEV_ERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
+    const uint32_t excl = lookback_excl(status, tile, tid, err);
     s_gbase[tid] = dbase + excl - tstart;
     volatile uint32_t* st = status + (size_t)tile * kRadix + tid;
     *st = kFlagPre | ((excl + tcount) & kValMask);
@@ -412,18 +348,6 @@ bits_status radix_sort_pairs(const uint2* d_src, uint32_t n, const SortSpec spec
     BITS_LAUNCH_CHECK("k_onesweep");
   }
   return BITS_OK;
-}
-
-bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, uint32_t* out_e,
-                                 uint32_t* d_err, RadixScratch& ws, cudaStream_t st) {
-  SortSpec spec[2]{};
-  spec[0].comp = 0;
-  spec[0].out_keys = out_s;
-  spec[0].tmp_keys = ws.tmp_s;
-  spec[1].comp = 1;
-  spec[1].out_keys = out_e;
-  spec[1].tmp_keys = ws.tmp_e;
-  return radix_sort_pairs(d_b, n, spec, 0, d_err, ws, st, nullptr);
 }
 
 }  // namespace bits

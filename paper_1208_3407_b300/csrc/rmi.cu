@@ -165,9 +165,8 @@ k_rmi_errors(const uint32_t* __restrict__ X, uint32_t n, float ra, float rb, uin
   }
 }
 
-constexpr int kCountBlock = 256;
-
-__global__ void __launch_bounds__(kCountBlock)
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
 k_count_rmi(const uint2* __restrict__ a, uint32_t n, LevelIndex L, RmiView R, uint32_t nb,
             uint32_t* __restrict__ counts, unsigned long long* __restrict__ total,
             uint32_t* __restrict__ err) {
@@ -198,8 +197,21 @@ k_count_rmi(const uint2* __restrict__ a, uint32_t n, LevelIndex L, RmiView R, ui
   if (threadIdx.x == 0 && sum) atomicAdd(total, sum);
 }
 
-int rmi_count_blocks_per_sm() {
-  return kernel_blocks_per_sm(reinterpret_cast<const void*>(k_count_rmi), kCountBlock, 0);
+template <int BLOCK>
+bits_status launch_rmi(const bits_db* db, const uint2* a, uint32_t n, uint32_t* d_counts,
+                       uint64_t* d_total, cudaStream_t st) {
+  const int per_sm =
+      kernel_blocks_per_sm(reinterpret_cast<const void*>(k_count_rmi<BLOCK>), BLOCK, 0);
+  const uint32_t need = (n + BLOCK - 1) / BLOCK;
+  const uint32_t grid = std::min<uint32_t>(need, (uint32_t)(per_sm * sm_count()));
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  pdl_config(cfg, attr, dim3(grid), dim3(BLOCK), 0, st);
+  BITS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_count_rmi<BLOCK>, a, n, db->lvl, rmi_view(db), db->n,
+                                   d_counts, reinterpret_cast<unsigned long long*>(d_total),
+                                   db->err));
+  BITS_LAUNCH_CHECK("k_count_rmi");
+  return BITS_OK;
 }
 
 }  // namespace
@@ -283,19 +295,14 @@ bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t
 }
 
 bits_status launch_count_rmi(const bits_db* db, const uint32_t* d_a, uint32_t n,
-                             uint32_t* d_counts, uint64_t* d_total, cudaStream_t st) {
+                             uint32_t* d_counts, uint64_t* d_total, cudaStream_t st,
+                             const TuneCount* tc) {
   bits_status s = launch_zero_total(d_total, st);
   if (s != BITS_OK || n == 0) return s;
-  const uint32_t need = (n + kCountBlock - 1) / kCountBlock;
-  const uint32_t grid = std::min<uint32_t>(need, (uint32_t)(rmi_count_blocks_per_sm() * sm_count()));
-  cudaLaunchConfig_t cfg;
-  cudaLaunchAttribute attr[1];
-  pdl_config(cfg, attr, dim3(grid), dim3(kCountBlock), 0, st);
-  BITS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_count_rmi, reinterpret_cast<const uint2*>(d_a), n,
-                                   db->lvl, rmi_view(db), db->n, d_counts,
-                                   reinterpret_cast<unsigned long long*>(d_total), db->err));
-  BITS_LAUNCH_CHECK("k_count_rmi");
-  return BITS_OK;
+  const int block = tc ? tc->block : count_params(db, BITS_METHOD_RMI, n, d_counts != nullptr).block;
+  const uint2* a = reinterpret_cast<const uint2*>(d_a);
+  return block == 512 ? launch_rmi<512>(db, a, n, d_counts, d_total, st)
+                      : launch_rmi<256>(db, a, n, d_counts, d_total, st);
 }
 
 }  // namespace bits

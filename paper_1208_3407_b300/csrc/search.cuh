@@ -29,7 +29,9 @@
 
 namespace bits {
 
-constexpr int kMaxLevels = 6;  // J <= 5 for n < 2^30 with a 8191-entry top
+constexpr int kMaxLevels = 8;  // levels 0 .. 7: a default top J <= 5, raised by at most 2
+constexpr int kMaxTop = 5;     // highest default top level (past it the top simply grows)
+constexpr int kTopRaise = 2;   // levels above the default top a launch may keep in shared memory
 
 struct LevelIndex {
   const uint32_t* x[2];               // the sorted arrays B_S, B_E (padded to 16)

@@ -86,6 +86,20 @@ def test_host_side_argument_checks(lib):
     # enumeration
     assert lib.bits_enumerate_offsets(None, None, 0, None, None) == _lib.BITS_EINVAL
     assert lib.bits_enumerate_pairs(None, None, 0, None, None, None) == _lib.BITS_EINVAL
+    # launch-parameter pins: validated on the host
+    bad = _lib.Tuning(3, 0, 0, 0, 0)
+    assert lib.bits_set_tuning(C.byref(bad)) == _lib.BITS_EINVAL
+    bad = _lib.Tuning(-1, 0, 128, 512, 0)
+    assert lib.bits_set_tuning(C.byref(bad)) == _lib.BITS_EINVAL
+    good = _lib.Tuning(1, 256, 128, 2048, 16384)
+    assert lib.bits_set_tuning(C.byref(good)) == _lib.BITS_OK
+    got = _lib.Tuning()
+    assert lib.bits_get_tuning(C.byref(got)) == _lib.BITS_OK
+    assert (got.top_raise, got.block, got.mc_shuffles, got.mc_chunk, got.ap_chunk) == \
+        (1, 256, 128, 2048, 16384)
+    assert lib.bits_set_tuning(None) == _lib.BITS_OK
+    assert lib.bits_get_tuning(C.byref(got)) == _lib.BITS_OK and got.top_raise == -1
+    assert lib.bits_get_tuning(None) == _lib.BITS_EINVAL
     lib.bits_free(None)
     assert lib.bits_kernel_launches() == 0
 

@@ -5,6 +5,9 @@
 Workloads (inputs from the seeded generator ``bits_synth``):
     count-200k-20m   bits_count, 200,000 queries vs 20,000,000 reads (exome-vs-reads)
     count-100m-100m  bits_count, 100M queries vs 100M intervals (learned index built)
+    count-10m-100m   the first 10M of those queries vs the same 100M intervals (a
+                     reduced case for multi-pass ncu captures; DRAM bytes per
+                     query scale with the queries)
     build-20m        bits_build_db of the 20,000,000 reads
     enumerate-200k-20m  every intersecting pair of those queries and reads
     mc-100k-1m       bits_mc, 100,000 intervals vs 1,000,000, 10,000 shuffles
@@ -58,11 +61,13 @@ def main(argv=None):
     args = ap.parse_args(argv)
     m = METHODS[args.method]
     ms = 0.0
-    if args.name in ("count-200k-20m", "count-100m-100m"):
+    if args.name in ("count-200k-20m", "count-100m-100m", "count-10m-100m"):
         if args.name == "count-200k-20m":
             _, a_np, b_np = bits_synth.config2()
         else:
             a_np, b_np = bits_synth.config4()
+            if args.name == "count-10m-100m":
+                a_np = a_np[:10_000_000]
         db = Database(_dev(b_np), rmi_leaves_log2=16)
         a = _dev(a_np)
         counts = torch.empty(a_np.shape[0], dtype=torch.uint32, device="cuda")
