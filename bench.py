@@ -451,10 +451,18 @@ def run_ours(args):
     counts_host = torch.zeros(n_mine, dtype=torch.uint32).pin_memory()
     total_host = torch.zeros(1, dtype=torch.uint64).pin_memory()
 
-    def e2e_step():
-        db4.count_host(a_host, counts=counts_host, total=total_host, method=head_m, check=False)
-
-    e2e_ms, e2e_launches, _ = timed(e2e_step, args.steps, args.warmup)
+    # Host buffers: the plain search and the learned index read and write
+    # them in place over the bus (merge path would stage them).  The faster
+    # of the plain search and the headline's method is reported.
+    e2e_forms = {}
+    for name, m in (("search_in_place", bits.METHOD_SEARCH), ("headline_method", head_m)):
+        if name == "headline_method" and head_m == bits.METHOD_SEARCH:
+            continue
+        ms, l, _ = timed(lambda m=m: db4.count_host(a_host, counts=counts_host, total=total_host,
+                                                     method=m, check=False), args.steps, args.warmup)
+        e2e_forms[name] = (ms, l)
+    e2e_name = min(e2e_forms, key=lambda k: e2e_forms[k][0])
+    e2e_ms, e2e_launches = e2e_forms[e2e_name]
     db4.check()
     parity["headline_host_buffers"] = bool(
         np.array_equal(counts_host.numpy(), c4.cpu().numpy()) and
@@ -566,8 +574,9 @@ def run_ours(args):
         "e2e": {"value": n4 / (e2e_ms * 1e-3), "unit": "queries/s",
                 "h2d_bytes_per_step": int(n4 * 8), "d2h_bytes_per_step": int(n4 * 4 + 8),
                 "ms_per_step": e2e_ms, "gpu_launches": e2e_launches,
-                "call": "bits_count_host on page-locked queries and counts (read and written in "
-                        "place by the search kernel over the bus) + the total copied back"},
+                "call": "bits_count_host on page-locked queries and counts (read and written "
+                        "in place by the search kernel over the bus) + the total copied back",
+                "form": e2e_name, "forms_ms": sig({k: v[0] for k, v in e2e_forms.items()})},
         "gpu_launches": launches,
         "clocks": clocks,
         "headline_form": head,

@@ -162,12 +162,7 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
       const int k = h * kH + kk;
       const uint32_t idx = warp_base + k * 32u + lane;
       const uint32_t d = idx < n ? ((key[k] >> shift) & 255u) : 256u;
-      unsigned peers = 0xFFFFFFFFu;
-      #pragma unroll
-      for (int b = 0; b < 9; ++b) {
-        const unsigned bb = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
-        peers &= ((d >> b) & 1u) ? bb : ~bb;
-      }
+      const unsigned peers = peers_of<9>(d);
       peers_k[kk] = peers;
       lead_base[kk] = 0u;
       if ((int)lane == __ffs(peers) - 1)

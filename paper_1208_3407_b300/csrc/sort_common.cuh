@@ -13,6 +13,22 @@ constexpr int kLookAhead = 8;  // status words one look-back thread reads per ro
 // this tile only, or inclusive prefix of all tiles up to it), count below.
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kValMask = (1u << 30) - 1;
 
+// Lanes of the warp whose digit d equals this lane's (all 32 lanes call it),
+// from BITS bit-sliced ballots: bit b of d is moved to the sign bit, the
+// ballot of the sign gives the lanes with that bit set, and the same sign
+// spread over the word (0 or all ones) selects the ballot or its complement.
+template <int BITS>
+__device__ __forceinline__ unsigned peers_of(uint32_t d) {
+  unsigned peers = 0xFFFFFFFFu;
+  #pragma unroll
+  for (int b = 0; b < BITS; ++b) {
+    const int x = (int)(d << (31 - b));
+    const unsigned bb = __ballot_sync(0xFFFFFFFFu, x < 0);
+    peers &= ~(bb ^ (unsigned)(x >> 31));
+  }
+  return peers;
+}
+
 // Exclusive scan of one value per thread over threads [0, 256); every
 // thread of the block must call it.
 __device__ __forceinline__ uint32_t scan256_excl(uint32_t v, uint32_t* s_w) {

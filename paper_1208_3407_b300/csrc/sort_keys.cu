@@ -248,16 +248,7 @@ k_sweep_keys(SkJobs J, uint32_t n, uint32_t* __restrict__ err) {
         const int k = h * kH + kk;
         const uint32_t pos = wbase + k * 32u + lane;
         const uint32_t d = pos < valid ? ((buf_l[pos] >> shift) & 255u) : (uint32_t)kRadix;
-        unsigned peers = 0xFFFFFFFFu;
-        #pragma unroll
-        for (int bt = 0; bt < 8; ++bt) {
-          const unsigned bb = __ballot_sync(0xFFFFFFFFu, (d >> bt) & 1u);
-          peers &= ((d >> bt) & 1u) ? bb : ~bb;
-        }
-        if (!full) {  // the empty lanes of a ragged tile carry digit 256
-          const unsigned bb = __ballot_sync(0xFFFFFFFFu, d >> 8);
-          peers &= (d >> 8) ? bb : ~bb;
-        }
+        const unsigned peers = full ? peers_of<8>(d) : peers_of<9>(d);
         peers_k[kk] = peers;
         lead[kk] = 0u;
         if ((int)lane == __ffs(peers) - 1) {

@@ -34,7 +34,7 @@ sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 import bits_synth  # noqa: E402
 
 from paper_1208_3407_b300 import (METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH,  # noqa: E402
-                                  Database, count_matrix, mc_matrix)
+                                  Database, count_matrix, mc_matrix, set_tuning)
 
 METHODS = {"search": METHOD_SEARCH, "rmi": METHOD_RMI, "mergepath": METHOD_MERGEPATH}
 
@@ -58,7 +58,14 @@ def main(argv=None):
     ap.add_argument("--method", default="search", choices=sorted(METHODS))
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--shuffles", type=int, default=4, help="shuffles per Monte-Carlo screen call")
+    ap.add_argument("--top-raise", type=int, default=0,
+                    help="pinned shared-memory top (no autotuning runs inside a profile)")
+    ap.add_argument("--block", type=int, default=512)
     args = ap.parse_args(argv)
+    # Profiles capture the kernels of one configuration: pin the launch
+    # parameters so that the autotuner times no candidates here.
+    set_tuning(top_raise=args.top_raise, block=args.block, mc_shuffles=256, mc_chunk=1024,
+               ap_chunk=8192)
     m = METHODS[args.method]
     ms = 0.0
     if args.name in ("count-200k-20m", "count-100m-100m", "count-10m-100m"):
