@@ -1,16 +1,24 @@
 // Learned index (two-stage RMI, Kraska et al. 2018) over each sorted array:
 // on-device fitting, and bits_count through it.
 //
-// Fitting, all on the device after the sort:
-//   1. k_rmi_root_sums: least-squares sums (fp64) of the key against the
-//      target leaf position i * 2^L / n; the host turns them into the fp32
-//      root (slope, intercept), slope clamped to >= 0 so the root is monotone.
-//   2. k_rmi_bounds: the slice [lo, hi) of ranks every leaf owns (contiguous
+// Fitting, all on the device after the sort.  Both stages are least-squares
+// lines of rank against key; their sums are exact integers (the part's fp64
+// rate is a small fraction of its integer rate, and exact sums lose nothing
+// to cancellation):
+//   1. k_rmi_chunk_moments: per chunk of kChunk consecutive ranks i, the
+//      sums of X_i, X_i^2 and i * X_i (64- and 128-bit integers).
+//   2. k_rmi_chunk_scan: exclusive prefix of those sums over the chunks, with
+//      the whole array's sums at the end.  The host fits the root from the
+//      whole-array sums and rounds it to fp32 (slope clamped to >= 0 so the
+//      root is monotone).
+//   3. k_rmi_bounds: the slice [lo, hi) of ranks every leaf owns (contiguous
 //      because the root is monotone).
-//   3. k_rmi_leaf_sums: per-leaf least-squares sums (fp64) of rank-in-slice
-//      against key - base, reduced by warp segments, one atomic per leaf run.
-//   4. k_rmi_fit: per-leaf fp32 slope (>= 0) and intercept.
-//   5. k_rmi_errors: with the search's own rmi_predict, the smallest and
+//   4. k_rmi_boundary_moments: the prefix sums at every slice boundary (the
+//      chunk prefix plus the ranks of the boundary's chunk below it).
+//   5. k_rmi_fit: a leaf's sums are differences of its two boundaries'
+//      prefixes; from them, exactly in 128-bit integers, the moments of
+//      (key - base, rank - lo), and the fp32 slope (>= 0) and intercept.
+//   6. k_rmi_errors: with the search's own rmi_predict, the smallest and
 //      largest (true rank - prediction) over every key of the slice (and one
 //      past each key), so that every query routed to the leaf has its rank in
 //      [prediction + err_lo, prediction + err_hi].
@@ -23,44 +31,142 @@
 namespace bits {
 namespace {
 
-constexpr int kRmiBlock = 256;
+using u64 = unsigned long long;
+using u128 = unsigned __int128;
+using i128 = __int128;
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+constexpr int kRmiBlock = 256;
+constexpr uint32_t kChunk = 1024;  // ranks per chunk of the moment prefix sums
+constexpr int kScanThreads = 1024;
+
+// Sums over a run of ranks i of the sorted array X.
+struct Moments {
+  u64 s1;   // sum of X_i             (< 2^62 for n < 2^30)
+  u128 s2;  // sum of X_i^2           (< 2^94)
+  u128 s3;  // sum of i * X_i         (< 2^92)
+};
+
+// Moments of a run stored as three arrays (16-byte aligned for the 128-bit ones).
+struct MomentArrays {
+  u64* s1;
+  u128* s2;
+  u128* s3;
+};
+
+__device__ __forceinline__ void add_key(Moments& m, uint32_t i, uint32_t x) {
+  m.s1 += x;
+  m.s2 += (u128)((u64)x * x);
+  m.s3 += (u128)((u64)i * x);
+}
+
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {
+  const u64 lo = __shfl_xor_sync(0xFFFFFFFFu, (u64)v, o);
+  const u64 hi = __shfl_xor_sync(0xFFFFFFFFu, (u64)(v >> 64), o);
+  return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ Moments warp_sum_moments(Moments m) {
   #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  return v;
+  for (int o = 16; o > 0; o >>= 1) {
+    m.s1 += __shfl_xor_sync(0xFFFFFFFFu, m.s1, o);
+    m.s2 += shfl_xor_u128(m.s2, o);
+    m.s3 += shfl_xor_u128(m.s3, o);
+  }
+  return m;
+}
+
+__device__ __forceinline__ void store_moments(const MomentArrays& A, size_t k, const Moments& m) {
+  A.s1[k] = m.s1;
+  A.s2[k] = m.s2;
+  A.s3[k] = m.s3;
+}
+
+__device__ __forceinline__ Moments load_moments(const MomentArrays& A, size_t k) {
+  return Moments{A.s1[k], A.s2[k], A.s3[k]};
+}
+
+// The nearest double to an exact 128-bit integer (two roundings at most).
+__device__ __forceinline__ double i128_to_double(i128 v) {
+  const bool neg = v < 0;
+  const u128 u = neg ? (u128)(-v) : (u128)v;
+  const double d = (double)(u64)(u >> 64) * 18446744073709551616.0 + (double)(u64)u;
+  return neg ? -d : d;
 }
 
 __global__ void __launch_bounds__(kRmiBlock)
-k_rmi_root_sums(const uint32_t* __restrict__ X, uint32_t n, double t_per_rank,
-                double* __restrict__ sums) {
-  __shared__ double s_red[4][kRmiBlock / 32];
-  const uint32_t x0 = X[0];
-  double sx = 0, st = 0, sxx = 0, sxt = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double x = (double)(X[i] - x0), t = (double)i * t_per_rank;
-    sx += x;
-    st += t;
-    sxx = fma(x, x, sxx);
-    sxt = fma(x, t, sxt);
+k_rmi_chunk_moments(const uint32_t* __restrict__ X, uint32_t n, MomentArrays chunks) {
+  __shared__ Moments s_w[kRmiBlock / 32];
+  const uint32_t base = blockIdx.x * kChunk;
+  Moments m{0ull, 0, 0};
+  #pragma unroll
+  for (uint32_t k = 0; k < kChunk / kRmiBlock; ++k) {
+    const uint32_t i = base + k * kRmiBlock + threadIdx.x;
+    if (i < n) add_key(m, i, X[i]);
   }
-  sx = warp_sum_d(sx);
-  st = warp_sum_d(st);
-  sxx = warp_sum_d(sxx);
-  sxt = warp_sum_d(sxt);
-  const unsigned w = threadIdx.x >> 5;
-  if (lane_id() == 0) {
-    s_red[0][w] = sx;
-    s_red[1][w] = st;
-    s_red[2][w] = sxx;
-    s_red[3][w] = sxt;
-  }
+  m = warp_sum_moments(m);
+  if (lane_id() == 0) s_w[threadIdx.x >> 5] = m;
   __syncthreads();
-  if (threadIdx.x < 4) {
-    double v = 0;
-    for (int k = 0; k < kRmiBlock / 32; ++k) v += s_red[threadIdx.x][k];
-    atomicAdd(sums + threadIdx.x, v);
+  if (threadIdx.x == 0) {
+    Moments t{0ull, 0, 0};
+    for (int w = 0; w < kRmiBlock / 32; ++w) {
+      t.s1 += s_w[w].s1;
+      t.s2 += s_w[w].s2;
+      t.s3 += s_w[w].s3;
+    }
+    store_moments(chunks, blockIdx.x, t);
   }
+}
+
+// One CTA: the chunk sums become exclusive prefixes in place, and entry
+// `nchunks` receives the sums over the whole array.  Thread t owns a
+// contiguous segment of chunks.
+__global__ void __launch_bounds__(kScanThreads)
+k_rmi_chunk_scan(MomentArrays chunks, uint32_t nchunks) {
+  __shared__ Moments s_w[kScanThreads / 32];
+  const uint32_t per = (nchunks + kScanThreads - 1) / kScanThreads;
+  const uint32_t b = min(nchunks, threadIdx.x * per), e = min(nchunks, b + per);
+  Moments own{0ull, 0, 0};
+  for (uint32_t k = b; k < e; ++k) {
+    const Moments c = load_moments(chunks, k);
+    own.s1 += c.s1;
+    own.s2 += c.s2;
+    own.s3 += c.s3;
+  }
+  // Exclusive scan of the segment sums over the block.
+  const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+  Moments inc = own;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u64 a1 = __shfl_up_sync(0xFFFFFFFFu, inc.s1, o);
+    const u64 a2l = __shfl_up_sync(0xFFFFFFFFu, (u64)inc.s2, o);
+    const u64 a2h = __shfl_up_sync(0xFFFFFFFFu, (u64)(inc.s2 >> 64), o);
+    const u64 a3l = __shfl_up_sync(0xFFFFFFFFu, (u64)inc.s3, o);
+    const u64 a3h = __shfl_up_sync(0xFFFFFFFFu, (u64)(inc.s3 >> 64), o);
+    if (lane >= (unsigned)o) {
+      inc.s1 += a1;
+      inc.s2 += ((u128)a2h << 64) | a2l;
+      inc.s3 += ((u128)a3h << 64) | a3l;
+    }
+  }
+  if (lane == 31) s_w[w] = inc;
+  __syncthreads();
+  Moments run{0ull, 0, 0};
+  for (unsigned v = 0; v < w; ++v) {
+    run.s1 += s_w[v].s1;
+    run.s2 += s_w[v].s2;
+    run.s3 += s_w[v].s3;
+  }
+  run.s1 += inc.s1 - own.s1;
+  run.s2 += inc.s2 - own.s2;
+  run.s3 += inc.s3 - own.s3;
+  for (uint32_t k = b; k < e; ++k) {
+    const Moments c = load_moments(chunks, k);
+    store_moments(chunks, k, run);
+    run.s1 += c.s1;
+    run.s2 += c.s2;
+    run.s3 += c.s3;
+  }
+  if (threadIdx.x == kScanThreads - 1) store_moments(chunks, nchunks, run);
 }
 
 __global__ void k_rmi_bounds(const uint32_t* __restrict__ X, uint32_t n, float ra, float rb,
@@ -72,44 +178,30 @@ __global__ void k_rmi_bounds(const uint32_t* __restrict__ X, uint32_t n, float r
   }
 }
 
+// One warp per slice boundary l in [0, nleaves]: the moment prefix at rank
+// p = lo[l] (sums over ranks [0, p)) = the prefix of p's chunk + the ranks
+// of that chunk below p.
 __global__ void __launch_bounds__(kRmiBlock)
-k_rmi_leaf_sums(const uint32_t* __restrict__ X, uint32_t n, float ra, float rb, uint32_t nleaves,
-                const uint32_t* __restrict__ lo, double* __restrict__ sums) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned lane = lane_id();
-  const bool valid = i < n;
-  uint32_t l = 0xFFFFFFFFu;
-  double v[4] = {0, 0, 0, 0};
-  if (valid) {
-    const uint32_t key = X[i];
-    l = rmi_root(ra, rb, key, nleaves);
-    const uint32_t first = lo[l];
-    const double x = (double)(key - X[first]), y = (double)(i - first);
-    v[0] = x;
-    v[1] = y;
-    v[2] = x * x;
-    v[3] = x * y;
-  }
-  // Segmented reduction: lanes of one leaf are contiguous (X sorted, root monotone).
-  #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t ol = __shfl_down_sync(0xFFFFFFFFu, l, off);
-    #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const double ov = __shfl_down_sync(0xFFFFFFFFu, v[k], off);
-      if (lane + off < 32 && ol == l) v[k] += ov;
-    }
-  }
-  const uint32_t pl = __shfl_up_sync(0xFFFFFFFFu, l, 1);
-  if (valid && (lane == 0 || pl != l)) {
-    #pragma unroll
-    for (int k = 0; k < 4; ++k) atomicAdd(sums + 4 * (size_t)l + k, v[k]);
+k_rmi_boundary_moments(const uint32_t* __restrict__ X, const uint32_t* __restrict__ lo,
+                       uint32_t nleaves, MomentArrays chunks, MomentArrays at) {
+  const uint32_t l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (l > nleaves) return;
+  const uint32_t p = lo[l], c = p / kChunk;
+  Moments m{0ull, 0, 0};
+  for (uint32_t i = c * kChunk + lane_id(); i < p; i += 32) add_key(m, i, X[i]);
+  m = warp_sum_moments(m);
+  if (lane_id() == 0) {
+    const Moments pre = load_moments(chunks, c);
+    m.s1 += pre.s1;
+    m.s2 += pre.s2;
+    m.s3 += pre.s3;
+    store_moments(at, l, m);
   }
 }
 
 __global__ void k_rmi_fit(const uint32_t* __restrict__ X, uint32_t n,
-                          const uint32_t* __restrict__ lo, const double* __restrict__ sums,
-                          uint32_t nleaves, bits_rmi_leaf* __restrict__ leaves) {
+                          const uint32_t* __restrict__ lo, MomentArrays at, uint32_t nleaves,
+                          bits_rmi_leaf* __restrict__ leaves) {
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < nleaves;
        l += gridDim.x * blockDim.x) {
     const uint32_t first = lo[l], last = lo[l + 1], cnt = last - first;
@@ -118,13 +210,23 @@ __global__ void k_rmi_fit(const uint32_t* __restrict__ X, uint32_t n,
     else if (n) base = X[n - 1];
     double slope = 0.0, icpt = 0.0;
     if (cnt >= 2) {
-      const double c = (double)cnt;
-      const double mx = sums[4 * (size_t)l] / c, my = sums[4 * (size_t)l + 1] / c;
-      const double vxx = sums[4 * (size_t)l + 2] / c - mx * mx;
-      const double cxy = sums[4 * (size_t)l + 3] / c - mx * my;
-      if (vxx > 0.0) slope = cxy / vxx;
+      // Sums over the slice of X_i, X_i^2, i * X_i, then of x = X_i - base
+      // and y = i - first (all exact):
+      //   Sx  = S1 - c base            Sy  = c (c - 1) / 2
+      //   Sxx = S2 - 2 base S1 + c base^2
+      //   Sxy = S3 - first S1 - base c (c - 1) / 2
+      const Moments hi = load_moments(at, l + 1), lw = load_moments(at, l);
+      const i128 c = cnt, bs = base, f = first;
+      const i128 s1 = (i128)(hi.s1 - lw.s1), s2 = (i128)(hi.s2 - lw.s2),
+                 s3 = (i128)(hi.s3 - lw.s3);
+      const i128 tri = c * (c - 1) / 2;
+      const i128 sx = s1 - c * bs, sy = tri;
+      const i128 sxx = s2 - 2 * bs * s1 + c * bs * bs;
+      const i128 sxy = s3 - f * s1 - bs * tri;
+      const i128 den = c * sxx - sx * sx, num = c * sxy - sx * sy;
+      if (den > 0) slope = i128_to_double(num) / i128_to_double(den);
       if (!(slope > 0.0)) slope = 0.0;
-      icpt = my - slope * mx;
+      icpt = (i128_to_double(sy) - slope * i128_to_double(sx)) / (double)cnt;
     }
     bits_rmi_leaf lf;
     lf.base_key = base;
@@ -229,18 +331,32 @@ RmiView rmi_view(const bits_db* db) {
 
 bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t st) {
   const uint32_t L = 1u << rmi.leaves_log2;
-  // scratch: 4 root sums | lo[L + 1] | leaf sums [L][4]
-  const size_t off_lo = 256;
-  const size_t off_sums = (off_lo + sizeof(uint32_t) * (L + 1) + 255) / 256 * 256;
-  const size_t bytes = off_sums + sizeof(double) * 4 * (size_t)L;
+  const uint32_t nchunks = (n + kChunk - 1) / kChunk;
+  // Scratch: chunk moments [nchunks + 1] | boundary moments [L + 1] | lo [L + 1].
+  auto arrays_bytes = [](size_t m) {
+    return (sizeof(u64) * m + 255) / 256 * 256 + 2 * ((sizeof(u128) * m + 255) / 256 * 256);
+  };
+  const size_t chunk_bytes = arrays_bytes((size_t)nchunks + 1);
+  const size_t at_bytes = arrays_bytes((size_t)L + 1);
+  const size_t bytes = chunk_bytes + at_bytes + sizeof(uint32_t) * ((size_t)L + 1);
   void* scratch = nullptr;
   {
     const bits_status as = pool_alloc(&scratch, bytes, st);
     if (as != BITS_OK) return as;
   }
-  double* root_sums = static_cast<double*>(scratch);
-  uint32_t* lo = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) + off_lo);
-  double* leaf_sums = reinterpret_cast<double*>(static_cast<char*>(scratch) + off_sums);
+  auto carve = [](char* p, size_t m) {
+    MomentArrays A;
+    A.s1 = reinterpret_cast<u64*>(p);
+    p += (sizeof(u64) * m + 255) / 256 * 256;
+    A.s2 = reinterpret_cast<u128*>(p);
+    p += (sizeof(u128) * m + 255) / 256 * 256;
+    A.s3 = reinterpret_cast<u128*>(p);
+    return A;
+  };
+  char* base = static_cast<char*>(scratch);
+  const MomentArrays chunks = carve(base, (size_t)nchunks + 1);
+  const MomentArrays at = carve(base + chunk_bytes, (size_t)L + 1);
+  uint32_t* lo = reinterpret_cast<uint32_t*>(base + chunk_bytes + at_bytes);
   auto done = [&](bits_status s) {
     pool_free(scratch, st);
     return s;
@@ -248,24 +364,38 @@ bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t
   if (cudaMemsetAsync(scratch, 0, bytes, st) != cudaSuccess)
     return done(cuda_status(cudaGetLastError(), "cudaMemsetAsync(rmi scratch)"));
 
+  if (n) {
+    k_rmi_chunk_moments<<<nchunks, kRmiBlock, 0, st>>>(X, n, chunks);
+    count_launch();
+  }
+  k_rmi_chunk_scan<<<1, kScanThreads, 0, st>>>(chunks, nchunks);
+  count_launch();
+
+  // Root: least-squares line of t = i * L / n against the key over the
+  // whole array, from its exact sums (host 128-bit integers):
+  //   slope_i = (n Sxi - Sx Si) / (n Sxx - Sx^2),  Si = n (n - 1) / 2.
   float ra = 0.f, rb = 0.f;
   if (n >= 2) {
-    const int grid = std::max(1, std::min<int>(sm_count() * 8, (n + kRmiBlock - 1) / kRmiBlock));
-    k_rmi_root_sums<<<grid, kRmiBlock, 0, st>>>(X, n, (double)L / (double)n, root_sums);
-    count_launch();
-    double h[4] = {0, 0, 0, 0};
-    uint32_t x0 = 0;
-    if (cudaMemcpyAsync(h, root_sums, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(&x0, X, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    u64 h1 = 0;
+    u128 h2 = 0, h3 = 0;
+    if (cudaMemcpyAsync(&h1, chunks.s1 + nchunks, sizeof(h1), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&h2, chunks.s2 + nchunks, sizeof(h2), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&h3, chunks.s3 + nchunks, sizeof(h3), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return done(cuda_status(cudaGetLastError(), "rmi root sums"));
-    const double c = (double)n;
-    const double den = c * h[2] - h[0] * h[0];
-    double a = den > 0 ? (c * h[3] - h[0] * h[1]) / den : 0.0;
+    const i128 c = n, sx = (i128)h1, sxx = (i128)h2, sxi = (i128)h3;
+    const i128 si = c * (c - 1) / 2;
+    const i128 den = c * sxx - sx * sx, num = c * sxi - sx * si;
+    const double scale = (double)L / (double)n;
+    double a = den > 0 ? (double)num / (double)den * scale : 0.0;
     if (!(a > 0.0) || !std::isfinite(a)) a = 0.0;
-    const double b = (h[1] - a * h[0]) / c;
+    // Intercept through the means: mean t = scale (n - 1) / 2, mean key = Sx / n.
+    const double b = scale * (double)(n - 1) / 2.0 - a * ((double)h1 / (double)n);
     ra = (float)a;
-    rb = (float)(b - a * (double)x0);
+    rb = (float)b;
     if (!std::isfinite(rb)) {
       ra = 0.f;
       rb = 0.f;
@@ -277,12 +407,10 @@ bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t
   const int gb = std::max(1, std::min<int>(sm_count() * 8, (n + 1 + 255) / 256));
   k_rmi_bounds<<<gb, 256, 0, st>>>(X, n, ra, rb, L, lo);
   count_launch();
-  if (n) {
-    const uint32_t blocks = (n + kRmiBlock - 1) / kRmiBlock;
-    k_rmi_leaf_sums<<<blocks, kRmiBlock, 0, st>>>(X, n, ra, rb, L, lo, leaf_sums);
-    count_launch();
-  }
-  k_rmi_fit<<<(L + 255) / 256, 256, 0, st>>>(X, n, lo, leaf_sums, L, rmi.leaves);
+  k_rmi_boundary_moments<<<((L + 1) * 32u + kRmiBlock - 1) / kRmiBlock, kRmiBlock, 0, st>>>(
+      X, lo, L, chunks, at);
+  count_launch();
+  k_rmi_fit<<<(L + 255) / 256, 256, 0, st>>>(X, n, lo, at, L, rmi.leaves);
   count_launch();
   if (n) {
     const uint32_t blocks = (n + kRmiBlock - 1) / kRmiBlock;
