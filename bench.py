@@ -136,7 +136,7 @@ def profiled_value(profile: str, field: str, sources):
 
 def mean_sd(xs):
     return {"mean": statistics.fmean(xs), "sd": statistics.stdev(xs) if len(xs) > 1 else 0.0,
-            "runs": len(xs)}
+            "runs": len(xs), "values": list(xs)}
 
 
 class ClockSampler:

@@ -392,6 +392,10 @@ bits_status bits_db_info(const bits_db* db, const uint32_t** d_bs, const uint32_
  * key k as lo + round(slope * (k - base_key) + icpt), clamped, with the true
  * rank inside [prediction + err_lo, prediction + err_hi]).  The root maps k
  * to leaf floor(root_slope * k + root_icpt), clamped to [0, n_leaves).
+ * bits_build_db fits both stages on the device as least-squares lines of
+ * rank against key, from exact integer sums over the sorted array, and then
+ * measures every leaf's error bounds with the search's own prediction, so
+ * counts through the index equal the plain search's whatever the fit.
  * The learned index is not in the paper; it narrows each BSearch of
  * Algorithm 1 before an exact search finishes it.  BITS_ENOTIMPL without one.
  */

@@ -9,8 +9,8 @@
 //     interval (each the start or the end word, plus a constant, exactly as
 //     the first pass derives them).
 //   * k_onesweep runs one digit pass for both key arrays in one launch.  A
-//     tile of 8192 keys is ranked stably inside the CTA (bit-sliced ballots
-//     and per-warp shared-memory counters), its per-digit counts are
+//     tile of 8192 keys is ranked stably inside the CTA (per-warp peer
+//     tables and digit counters in shared memory), its per-digit counts are
 //     published to a decoupled look-back table, and the CTA gathers the
 //     exclusive prefix of earlier tiles from that table (sort_common.cuh).
 //     Keys and values are staged in digit order in shared memory so that
@@ -38,6 +38,7 @@ constexpr int kSwWarps = kSwBlock / 32;
 constexpr int kSwKpt = 16;
 constexpr int kSwTile = kSwBlock * kSwKpt;  // 8192 keys
 static_assert(kSwTile == (int)kRadixTileKeys, "tile size shared with the look-back sizing");
+static_assert(kSwWarps * kPeerTableWords <= kSwTile, "peer tables fit in the staging area");
 constexpr int kCnt = kRadix + 1;  // per-warp counters: 256 digits + the tail's empty lanes
 
 // validate: 0 = database (end > start required, else DEV_ERR_INVALID),
@@ -119,6 +120,7 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
   const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   if (tid == 0) *s_tile = atomicAdd(ticket, 1u);
   for (int i = tid; i < kSwWarps * kCnt; i += kSwBlock) s_wcnt[i] = 0u;
+  for (int i = tid; i < kSwWarps * kPeerTableWords; i += kSwBlock) s_stage[i] = 0u;
   const uint32_t hcount = tid < kRadix ? hist[tid] : 0u;
   const uint32_t dbase = scan256_excl(hcount, s_w);  // also publishes *s_tile / s_wcnt
   if (tid < kRadix) s_dbase[tid] = dbase;
@@ -144,10 +146,10 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
 
   // Stable rank of every key among the keys of its warp with the same digit
   // (< 32 * kSwKpt, so two 16-bit ranks share a register).  The lanes that
-  // share a digit come from eight bit-sliced ballots (a ninth separates the
-  // tail's empty lanes, which use digit 256); the lowest of them adds their
-  // number to the warp's counter with one shared-memory atomic and passes
-  // the old value on.  The atomics of one warp are performed in program
+  // share a digit come from the warp's peer table (sort_common.cuh; the
+  // tail's empty lanes use digit 256), kept in the staging area until the
+  // tile is staged; the lowest of them adds their number to the warp's
+  // counter with one shared-memory atomic and passes the old value on.  The atomics of one warp are performed in program
   // order, so ranks follow key order within the warp.
   uint32_t rank2[kSwKpt / 2];
   #pragma unroll
@@ -162,7 +164,7 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
       const int k = h * kH + kk;
       const uint32_t idx = warp_base + k * 32u + lane;
       const uint32_t d = idx < n ? ((key[k] >> shift) & 255u) : 256u;
-      const unsigned peers = peers_of<9>(d);
+      const unsigned peers = peers_by_table(s_stage + w * kPeerTableWords, d);
       peers_k[kk] = peers;
       lead_base[kk] = 0u;
       if ((int)lane == __ffs(peers) - 1)

@@ -13,19 +13,23 @@ constexpr int kLookAhead = 8;  // status words one look-back thread reads per ro
 // this tile only, or inclusive prefix of all tiles up to it), count below.
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kValMask = (1u << 30) - 1;
 
-// Lanes of the warp whose digit d equals this lane's (all 32 lanes call it),
-// from BITS bit-sliced ballots: bit b of d is moved to the sign bit, the
-// ballot of the sign gives the lanes with that bit set, and the same sign
-// spread over the word (0 or all ones) selects the ballot or its complement.
-template <int BITS>
-__device__ __forceinline__ unsigned peers_of(uint32_t d) {
-  unsigned peers = 0xFFFFFFFFu;
-  #pragma unroll
-  for (int b = 0; b < BITS; ++b) {
-    const int x = (int)(d << (31 - b));
-    const unsigned bb = __ballot_sync(0xFFFFFFFFu, x < 0);
-    peers &= ~(bb ^ (unsigned)(x >> 31));
-  }
+// Words of one warp's peer table: a word per digit, 256 digits plus the
+// tail's empty lanes (digit 256), padded.
+constexpr int kPeerTableWords = 260;
+
+// Lanes of the warp whose digit d equals this lane's (all 32 lanes call it
+// together).  `tab` is the warp's peer table in shared memory, zero on entry
+// and left zero: every lane ORs its bit into the word of its digit, reads the
+// word back once all have, and clears it.  Three shared-memory operations
+// per key instead of eight ballots and their bit arithmetic, which kept the
+// integer pipe of the sort passes saturated.
+__device__ __forceinline__ unsigned peers_by_table(uint32_t* tab, uint32_t d) {
+  atomicOr(tab + d, 1u << lane_id());
+  __syncwarp();
+  const unsigned peers = tab[d];
+  __syncwarp();
+  tab[d] = 0u;
+  __syncwarp();
   return peers;
 }
 

@@ -16,11 +16,11 @@
 //     completion on an mbarrier), so the keys of a tile are never waited for
 //     in registers.  Three tile buffers rotate: the tile being ranked, the
 //     tile in flight, and the staging area in which the ranked tile is laid
-//     out in digit order.  Ranking is stable: per key eight (nine in a
-//     ragged last tile) bit-sliced ballots find the lanes with the same
-//     digit, whose lowest lane adds their number to the warp's 16-bit
-//     counter of that digit (two digits per 32-bit word); warps then take
-//     exclusive offsets per digit.  A tile publishes its digit counts at
+//     out in digit order.  Ranking is stable: the lanes with the same digit
+//     come from the warp's peer table (sort_common.cuh), kept in the staging
+//     slot while it is free; their lowest lane adds their number to the
+//     warp's 16-bit counter of that digit (two digits per 32-bit word);
+//     warps then take exclusive offsets per digit.  A tile publishes its digit counts at
 //     once and gathers the prefix of earlier tiles by decoupled look-back
 //     (sort_common.cuh); the staged keys then go out in runs of one digit.
 //     Every wait is bounded (DEV_ERR_TIMEOUT), and a scatter index outside
@@ -56,6 +56,7 @@ constexpr int kOffTix = kOffScan + 8;                       // [2] tickets (curr
 constexpr int kOffBar = kOffTix + 2;                        // [3] mbarriers, 8 bytes each
 constexpr int kSmemWords = kOffBar + 2 * kSkBufs;
 static_assert(kOffBar % 2 == 0, "mbarriers need 8-byte alignment");
+static_assert(kSkWarps * kPeerTableWords <= kSkTile, "peer tables fit in a tile slot");
 constexpr size_t kSmemBytes = sizeof(uint32_t) * kSmemWords;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -228,6 +229,8 @@ k_sweep_keys(SkJobs J, uint32_t n, uint32_t* __restrict__ err) {
       for (uint32_t i = tid; i < valid; i += kSkBlock) buf_l[i] = in[base + i];
     }
     for (uint32_t i = tid; i < (uint32_t)(kSkWarps * kSkCntWords); i += kSkBlock) s_cnt[i] = 0u;
+    // The staging slot holds the warps' peer tables until the tile is staged.
+    for (uint32_t i = tid; i < (uint32_t)(kSkWarps * kPeerTableWords); i += kSkBlock) buf_s[i] = 0u;
     __syncthreads();
 
     // Stable rank of each key among the keys of its warp with the same digit
@@ -248,7 +251,7 @@ k_sweep_keys(SkJobs J, uint32_t n, uint32_t* __restrict__ err) {
         const int k = h * kH + kk;
         const uint32_t pos = wbase + k * 32u + lane;
         const uint32_t d = pos < valid ? ((buf_l[pos] >> shift) & 255u) : (uint32_t)kRadix;
-        const unsigned peers = full ? peers_of<8>(d) : peers_of<9>(d);
+        const unsigned peers = peers_by_table(buf_s + w * kPeerTableWords, d);
         peers_k[kk] = peers;
         lead[kk] = 0u;
         if ((int)lane == __ffs(peers) - 1) {
