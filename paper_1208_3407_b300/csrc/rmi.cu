@@ -5,16 +5,20 @@
 // lines of rank against key; their sums are exact integers (the part's fp64
 // rate is a small fraction of its integer rate, and exact sums lose nothing
 // to cancellation):
-//   1. k_rmi_chunk_moments: per chunk of kChunk consecutive ranks i, the
-//      sums of X_i, X_i^2 and i * X_i (64- and 128-bit integers).
-//   2. k_rmi_chunk_scan: exclusive prefix of those sums over the chunks, with
-//      the whole array's sums at the end.  The host fits the root from the
+//   1. k_rmi_chunk_moments: per chunk of kChunk consecutive ranks i (one
+//      warp each), the sums of X_i, X_i^2 and i * X_i (64- and 128-bit
+//      integers).
+//   2. k_rmi_scan_block, twice: exclusive prefix of those sums, first within
+//      each group of 1024 chunks, then over the groups, with the whole
+//      array's sums at the end.  The host fits the root from the
 //      whole-array sums and rounds it to fp32 (slope clamped to >= 0 so the
 //      root is monotone).
-//   3. k_rmi_bounds: the slice [lo, hi) of ranks every leaf owns (contiguous
-//      because the root is monotone).
+//   3. k_rmi_bounds: the slice [lo, hi) of ranks every leaf owns, by a
+//      binary search per leaf boundary (the root is monotone, so the leaf of
+//      X_i never decreases with i).
 //   4. k_rmi_boundary_moments: the prefix sums at every slice boundary (the
-//      chunk prefix plus the ranks of the boundary's chunk below it).
+//      group and chunk prefixes plus the ranks of the boundary's chunk below
+//      it).
 //   5. k_rmi_fit: a leaf's sums are differences of its two boundaries'
 //      prefixes; from them, exactly in 128-bit integers, the moments of
 //      (key - base, rank - lo), and the fp32 slope (>= 0) and intercept.
@@ -93,46 +97,35 @@ __device__ __forceinline__ double i128_to_double(i128 v) {
   return neg ? -d : d;
 }
 
+// One warp per chunk: lane j adds ranks chunk * kChunk + j + 32 k.
 __global__ void __launch_bounds__(kRmiBlock)
-k_rmi_chunk_moments(const uint32_t* __restrict__ X, uint32_t n, MomentArrays chunks) {
-  __shared__ Moments s_w[kRmiBlock / 32];
-  const uint32_t base = blockIdx.x * kChunk;
+k_rmi_chunk_moments(const uint32_t* __restrict__ X, uint32_t n, uint32_t nchunks,
+                    MomentArrays chunks) {
+  const uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= nchunks) return;
+  const uint32_t base = c * kChunk;
   Moments m{0ull, 0, 0};
-  #pragma unroll
-  for (uint32_t k = 0; k < kChunk / kRmiBlock; ++k) {
-    const uint32_t i = base + k * kRmiBlock + threadIdx.x;
-    if (i < n) add_key(m, i, X[i]);
+  if (base + kChunk <= n) {
+    #pragma unroll 8
+    for (uint32_t k = 0; k < kChunk / 32; ++k) {
+      const uint32_t i = base + k * 32 + lane_id();
+      add_key(m, i, __ldcs(X + i));
+    }
+  } else {
+    for (uint32_t i = base + lane_id(); i < n; i += 32) add_key(m, i, X[i]);
   }
   m = warp_sum_moments(m);
-  if (lane_id() == 0) s_w[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    Moments t{0ull, 0, 0};
-    for (int w = 0; w < kRmiBlock / 32; ++w) {
-      t.s1 += s_w[w].s1;
-      t.s2 += s_w[w].s2;
-      t.s3 += s_w[w].s3;
-    }
-    store_moments(chunks, blockIdx.x, t);
-  }
+  if (lane_id() == 0) store_moments(chunks, c, m);
 }
 
-// One CTA: the chunk sums become exclusive prefixes in place, and entry
-// `nchunks` receives the sums over the whole array.  Thread t owns a
-// contiguous segment of chunks.
+// Items [b * 1024, min(count, (b + 1) * 1024)) of CTA b become exclusive
+// prefixes (within the CTA's group) in place; the group's total goes to
+// totals[b].
 __global__ void __launch_bounds__(kScanThreads)
-k_rmi_chunk_scan(MomentArrays chunks, uint32_t nchunks) {
+k_rmi_scan_block(MomentArrays items, uint32_t count, MomentArrays totals) {
   __shared__ Moments s_w[kScanThreads / 32];
-  const uint32_t per = (nchunks + kScanThreads - 1) / kScanThreads;
-  const uint32_t b = min(nchunks, threadIdx.x * per), e = min(nchunks, b + per);
-  Moments own{0ull, 0, 0};
-  for (uint32_t k = b; k < e; ++k) {
-    const Moments c = load_moments(chunks, k);
-    own.s1 += c.s1;
-    own.s2 += c.s2;
-    own.s3 += c.s3;
-  }
-  // Exclusive scan of the segment sums over the block.
+  const uint32_t k = blockIdx.x * kScanThreads + threadIdx.x;
+  const Moments own = k < count ? load_moments(items, k) : Moments{0ull, 0, 0};
   const unsigned lane = lane_id(), w = threadIdx.x >> 5;
   Moments inc = own;
   #pragma unroll
@@ -159,42 +152,50 @@ k_rmi_chunk_scan(MomentArrays chunks, uint32_t nchunks) {
   run.s1 += inc.s1 - own.s1;
   run.s2 += inc.s2 - own.s2;
   run.s3 += inc.s3 - own.s3;
-  for (uint32_t k = b; k < e; ++k) {
-    const Moments c = load_moments(chunks, k);
-    store_moments(chunks, k, run);
-    run.s1 += c.s1;
-    run.s2 += c.s2;
-    run.s3 += c.s3;
+  if (k < count) store_moments(items, k, run);
+  if (threadIdx.x == kScanThreads - 1) {
+    run.s1 += own.s1;
+    run.s2 += own.s2;
+    run.s3 += own.s3;
+    store_moments(totals, blockIdx.x, run);
   }
-  if (threadIdx.x == kScanThreads - 1) store_moments(chunks, nchunks, run);
 }
 
+// lo[l] = the first rank whose key the root sends to leaf l or above (n if
+// none): a binary search per boundary l in [0, nleaves].
 __global__ void k_rmi_bounds(const uint32_t* __restrict__ X, uint32_t n, float ra, float rb,
                              uint32_t nleaves, uint32_t* __restrict__ lo_out) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
-    const int prev = i == 0 ? -1 : (int)rmi_root(ra, rb, X[i - 1], nleaves);
-    const int cur = i == n ? (int)nleaves : (int)rmi_root(ra, rb, X[i], nleaves);
-    for (int l = prev + 1; l <= cur; ++l) lo_out[l] = i;
+  const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l > nleaves) return;
+  uint32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (rmi_root(ra, rb, X[mid], nleaves) >= l) hi = mid;
+    else lo = mid + 1;
   }
+  lo_out[l] = lo;
 }
 
 // One warp per slice boundary l in [0, nleaves]: the moment prefix at rank
-// p = lo[l] (sums over ranks [0, p)) = the prefix of p's chunk + the ranks
-// of that chunk below p.
+// p = lo[l] (sums over ranks [0, p)) = the prefix of the group of p's chunk
+// + the prefix of the chunk within its group + the ranks of the chunk below
+// p.  A boundary at p = n with n a multiple of kChunk takes the last chunk
+// whole (n >= 1 here).
 __global__ void __launch_bounds__(kRmiBlock)
 k_rmi_boundary_moments(const uint32_t* __restrict__ X, const uint32_t* __restrict__ lo,
-                       uint32_t nleaves, MomentArrays chunks, MomentArrays at) {
+                       uint32_t nleaves, uint32_t nchunks, MomentArrays chunks,
+                       MomentArrays groups, MomentArrays at) {
   const uint32_t l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (l > nleaves) return;
-  const uint32_t p = lo[l], c = p / kChunk;
+  const uint32_t p = lo[l], c = min(p / kChunk, nchunks - 1);
   Moments m{0ull, 0, 0};
   for (uint32_t i = c * kChunk + lane_id(); i < p; i += 32) add_key(m, i, X[i]);
   m = warp_sum_moments(m);
   if (lane_id() == 0) {
-    const Moments pre = load_moments(chunks, c);
-    m.s1 += pre.s1;
-    m.s2 += pre.s2;
-    m.s3 += pre.s3;
+    const Moments g = load_moments(groups, c / kScanThreads), pre = load_moments(chunks, c);
+    m.s1 += g.s1 + pre.s1;
+    m.s2 += g.s2 + pre.s2;
+    m.s3 += g.s3 + pre.s3;
     store_moments(at, l, m);
   }
 }
@@ -241,30 +242,76 @@ __global__ void k_rmi_fit(const uint32_t* __restrict__ X, uint32_t n,
   }
 }
 
+// Each thread takes kErrKeys consecutive ranks (usually all in one leaf): it
+// folds their errors per leaf run, sends any run that ends inside its ranks
+// straight to the leaf with atomics, and the run it ends on is combined with
+// the other lanes' last runs of the same leaf before one lane sends it.
+constexpr uint32_t kErrKeys = 8;
+
+__device__ __forceinline__ void send_errors(bits_rmi_leaf* leaves, uint32_t l, int mn, int mx) {
+  if (mn < 0) atomicMin(&leaves[l].err_lo, mn);
+  if (mx > 0) atomicMax(&leaves[l].err_hi, mx);
+}
+
 __global__ void __launch_bounds__(kRmiBlock)
 k_rmi_errors(const uint32_t* __restrict__ X, uint32_t n, float ra, float rb, uint32_t nleaves,
              bits_rmi_leaf* __restrict__ leaves) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = i < n;
-  uint32_t l = 0xFFFFFFFFu;
+  const uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) * kErrKeys;
+  uint32_t l = 0xFFFFFFFFu;  // leaf of the current run (none yet)
   int e_lo = 0x7FFFFFFF, e_hi = -0x7FFFFFFF;
-  if (valid) {
-    const uint32_t key = X[i];
-    l = rmi_root(ra, rb, key, nleaves);
-    const bits_rmi_leaf lf = leaves[l];
-    const uint32_t cnt = lf.hi - lf.lo;
-    const int p = rmi_predict(lf.slope, lf.icpt, lf.base_key, cnt, key);
-    const int local = (int)(i - lf.lo);
-    e_hi = local + 1 - p;  // a query just above key has rank i + 1
-    if (i == lf.lo || X[i - 1] != key) e_lo = local - p;  // rank of key itself
+  if (i0 < n) {
+    uint32_t key[kErrKeys];
+    const uint32_t m = min(kErrKeys, n - i0);
+    if (m == kErrKeys && (reinterpret_cast<uintptr_t>(X + i0) & 15u) == 0) {
+      const uint4 v0 = __ldcs(reinterpret_cast<const uint4*>(X + i0));
+      const uint4 v1 = __ldcs(reinterpret_cast<const uint4*>(X + i0) + 1);
+      key[0] = v0.x; key[1] = v0.y; key[2] = v0.z; key[3] = v0.w;
+      key[4] = v1.x; key[5] = v1.y; key[6] = v1.z; key[7] = v1.w;
+    } else {
+      #pragma unroll
+      for (uint32_t j = 0; j < kErrKeys; ++j) key[j] = j < m ? X[i0 + j] : 0u;
+    }
+    uint32_t prev = i0 > 0 ? X[i0 - 1] : 0u;
+    float slope = 0.f, icpt = 0.f;
+    uint32_t base = 0, lo = 0, cnt = 0;
+    #pragma unroll
+    for (uint32_t j = 0; j < kErrKeys; ++j) {
+      if (j < m) {
+        const uint32_t i = i0 + j, k = key[j];
+        const uint32_t lk = rmi_root(ra, rb, k, nleaves);
+        if (lk != l) {
+          if (l != 0xFFFFFFFFu) send_errors(leaves, l, e_lo, e_hi);
+          l = lk;
+          const bits_rmi_leaf lf = leaves[l];
+          slope = lf.slope;
+          icpt = lf.icpt;
+          base = lf.base_key;
+          lo = lf.lo;
+          cnt = lf.hi - lf.lo;
+          e_lo = 0x7FFFFFFF;
+          e_hi = -0x7FFFFFFF;
+        }
+        const int p = rmi_predict(slope, icpt, base, cnt, k);
+        const int local = (int)(i - lo);
+        e_hi = max(e_hi, local + 1 - p);  // a query just above k has rank i + 1
+        if (i == lo || prev != k) e_lo = min(e_lo, local - p);  // rank of k itself
+        prev = k;
+      }
+    }
   }
-  const unsigned peers = __match_any_sync(0xFFFFFFFFu, l);
+  // Lanes hold consecutive ranks, so the lanes that end on one leaf are a
+  // contiguous run: from this lane's run head up to the next head.
+  const unsigned lane = lane_id();
+  const uint32_t prev_l = __shfl_up_sync(0xFFFFFFFFu, l, 1);
+  const unsigned heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev_l != l);
+  const unsigned below = heads & (0xFFFFFFFFu >> (31 - lane));  // heads at or below this lane
+  const unsigned above = heads & ~(0xFFFFFFFFu >> (31 - lane));  // heads above this lane
+  const int first_lane = 31 - __clz(below);
+  const unsigned end_mask = above ? (above & (0u - above)) - 1u : 0xFFFFFFFFu;
+  const unsigned peers = end_mask & ~((1u << first_lane) - 1u);
   const int mn = __reduce_min_sync(peers, e_lo);
   const int mx = __reduce_max_sync(peers, e_hi);
-  if (valid && (int)lane_id() == __ffs(peers) - 1) {
-    if (mn < 0) atomicMin(&leaves[l].err_lo, mn);
-    if (mx > 0) atomicMax(&leaves[l].err_hi, mx);
-  }
+  if (l != 0xFFFFFFFFu && (int)lane == first_lane) send_errors(leaves, l, mn, mx);
 }
 
 template <int BLOCK>
@@ -332,13 +379,16 @@ RmiView rmi_view(const bits_db* db) {
 bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t st) {
   const uint32_t L = 1u << rmi.leaves_log2;
   const uint32_t nchunks = (n + kChunk - 1) / kChunk;
-  // Scratch: chunk moments [nchunks + 1] | boundary moments [L + 1] | lo [L + 1].
+  const uint32_t ngroups = (nchunks + kScanThreads - 1) / kScanThreads;  // <= 1024 (n < 2^30)
+  // Scratch: chunk moments [nchunks] | group moments [ngroups + 1] |
+  // boundary moments [L + 1] | lo [L + 1].
   auto arrays_bytes = [](size_t m) {
     return (sizeof(u64) * m + 255) / 256 * 256 + 2 * ((sizeof(u128) * m + 255) / 256 * 256);
   };
   const size_t chunk_bytes = arrays_bytes((size_t)nchunks + 1);
+  const size_t group_bytes = arrays_bytes((size_t)ngroups + 1);
   const size_t at_bytes = arrays_bytes((size_t)L + 1);
-  const size_t bytes = chunk_bytes + at_bytes + sizeof(uint32_t) * ((size_t)L + 1);
+  const size_t bytes = chunk_bytes + group_bytes + at_bytes + sizeof(uint32_t) * ((size_t)L + 1);
   void* scratch = nullptr;
   {
     const bits_status as = pool_alloc(&scratch, bytes, st);
@@ -355,8 +405,9 @@ bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t
   };
   char* base = static_cast<char*>(scratch);
   const MomentArrays chunks = carve(base, (size_t)nchunks + 1);
-  const MomentArrays at = carve(base + chunk_bytes, (size_t)L + 1);
-  uint32_t* lo = reinterpret_cast<uint32_t*>(base + chunk_bytes + at_bytes);
+  const MomentArrays groups = carve(base + chunk_bytes, (size_t)ngroups + 1);
+  const MomentArrays at = carve(base + chunk_bytes + group_bytes, (size_t)L + 1);
+  uint32_t* lo = reinterpret_cast<uint32_t*>(base + chunk_bytes + group_bytes + at_bytes);
   auto done = [&](bits_status s) {
     pool_free(scratch, st);
     return s;
@@ -365,11 +416,19 @@ bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t
     return done(cuda_status(cudaGetLastError(), "cudaMemsetAsync(rmi scratch)"));
 
   if (n) {
-    k_rmi_chunk_moments<<<nchunks, kRmiBlock, 0, st>>>(X, n, chunks);
+    const uint32_t warps_per_block = kRmiBlock / 32;
+    k_rmi_chunk_moments<<<(nchunks + warps_per_block - 1) / warps_per_block, kRmiBlock, 0, st>>>(
+        X, n, nchunks, chunks);
+    count_launch();
+    k_rmi_scan_block<<<ngroups, kScanThreads, 0, st>>>(chunks, nchunks, groups);
+    count_launch();
+    MomentArrays grand = groups;  // entry ngroups: the whole array
+    grand.s1 += ngroups;
+    grand.s2 += ngroups;
+    grand.s3 += ngroups;
+    k_rmi_scan_block<<<1, kScanThreads, 0, st>>>(groups, ngroups, grand);
     count_launch();
   }
-  k_rmi_chunk_scan<<<1, kScanThreads, 0, st>>>(chunks, nchunks);
-  count_launch();
 
   // Root: least-squares line of t = i * L / n against the key over the
   // whole array, from its exact sums (host 128-bit integers):
@@ -378,11 +437,11 @@ bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t
   if (n >= 2) {
     u64 h1 = 0;
     u128 h2 = 0, h3 = 0;
-    if (cudaMemcpyAsync(&h1, chunks.s1 + nchunks, sizeof(h1), cudaMemcpyDeviceToHost, st) !=
+    if (cudaMemcpyAsync(&h1, groups.s1 + ngroups, sizeof(h1), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
-        cudaMemcpyAsync(&h2, chunks.s2 + nchunks, sizeof(h2), cudaMemcpyDeviceToHost, st) !=
+        cudaMemcpyAsync(&h2, groups.s2 + ngroups, sizeof(h2), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
-        cudaMemcpyAsync(&h3, chunks.s3 + nchunks, sizeof(h3), cudaMemcpyDeviceToHost, st) !=
+        cudaMemcpyAsync(&h3, groups.s3 + ngroups, sizeof(h3), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return done(cuda_status(cudaGetLastError(), "rmi root sums"));
@@ -404,17 +463,19 @@ bits_status rmi_build(const uint32_t* X, uint32_t n, bits_rmi& rmi, cudaStream_t
   rmi.root_slope = ra;
   rmi.root_icpt = rb;
 
-  const int gb = std::max(1, std::min<int>(sm_count() * 8, (n + 1 + 255) / 256));
-  k_rmi_bounds<<<gb, 256, 0, st>>>(X, n, ra, rb, L, lo);
+  k_rmi_bounds<<<(L + 1 + 255) / 256, 256, 0, st>>>(X, n, ra, rb, L, lo);
   count_launch();
-  k_rmi_boundary_moments<<<((L + 1) * 32u + kRmiBlock - 1) / kRmiBlock, kRmiBlock, 0, st>>>(
-      X, lo, L, chunks, at);
-  count_launch();
+  if (n) {
+    k_rmi_boundary_moments<<<((L + 1) * 32u + kRmiBlock - 1) / kRmiBlock, kRmiBlock, 0, st>>>(
+        X, lo, L, nchunks, chunks, groups, at);
+    count_launch();
+  }
   k_rmi_fit<<<(L + 255) / 256, 256, 0, st>>>(X, n, lo, at, L, rmi.leaves);
   count_launch();
   if (n) {
-    const uint32_t blocks = (n + kRmiBlock - 1) / kRmiBlock;
-    k_rmi_errors<<<blocks, kRmiBlock, 0, st>>>(X, n, ra, rb, L, rmi.leaves);
+    const uint32_t threads = (n + kErrKeys - 1) / kErrKeys;
+    k_rmi_errors<<<(threads + kRmiBlock - 1) / kRmiBlock, kRmiBlock, 0, st>>>(X, n, ra, rb, L,
+                                                                            rmi.leaves);
     count_launch();
   }
   cudaError_t e = cudaGetLastError();
