@@ -19,12 +19,12 @@ projection, enumeration), the 64 x 32 all-pairs count and Monte-Carlo
 screen, the 100M database build, the headline's forms, and the Monte-Carlo
 significance test (100,000 intervals vs 1,000,000, 10,000 shuffles per
 launch: shuffles/s, placements/s, its L2 and issue rooflines).  Parity is
-checked in the run: every headline count of a 1M-query sample and the
+checked in the run: every headline count of a 4M-query sample and the
 sorted arrays against the CPU oracle, all 10,000 Monte-Carlo totals and all
 2,048 all-pairs totals against the oracle's stored values.
 
 The CPU oracle is timed on this host (rank 0) by the protocol both arms
-share: count of a 1,000,000-query sample of the headline against the
+share: count of a 4,000,000-query sample of the headline against the
 oracle-sorted database with all cores, of a 200,000-query sample
 single-threaded, and the oracle's database sort (std::sort) of 10,000,000
 of its intervals, each as mean and sd over 5 runs.
@@ -61,7 +61,7 @@ METRIC = "queries/s and MC shuffles/s on 1 B300, learned-index vs binary-search,
 HEADLINE = ("learned-index BITS at scale: 100,000,000 uniform queries vs 100,000,000 intervals "
             "(80% from 1000 Gaussians sigma U[1e3,1e6], 20% uniform) on a 3.0 Gbp line, lengths "
             "log-uniform [50,1e4], 2^16 linear leaves per sorted array")
-SAMPLE_ALL, SAMPLE_ONE, SAMPLE_BUILD, PROTOCOL_RUNS = 1_000_000, 200_000, 10_000_000, 5
+SAMPLE_ALL, SAMPLE_ONE, SAMPLE_BUILD, PROTOCOL_RUNS = 4_000_000, 200_000, 10_000_000, 5
 
 
 def config_dict(world: int) -> dict:
@@ -202,7 +202,7 @@ class ClockSampler:
 # ------------------------------------------------------------- the oracle protocol
 
 def oracle_protocol(o, a4, b4, bs4, be4, cores: int) -> dict:
-    """Both arms time the CPU oracle this way: count of a 1M-query sample of
+    """Both arms time the CPU oracle this way: count of a 4M-query sample of
     the headline against the oracle-sorted 100M database with all cores and
     of a 200k sample single-threaded, and the oracle's sort of 10M of the
     database's intervals (single-threaded std::sort of both words), each 5
@@ -434,7 +434,7 @@ def run_ours(args):
         int(t4.cpu().numpy()[0])
 
     # Parity of the headline against the oracle: the sorted arrays, and every
-    # count of the first 1M queries (the oracle sorts the database itself).
+    # count of the first 4M queries (the oracle sorts the database itself).
     parity = {}
     bs4 = be4 = None
     if lead:
@@ -444,7 +444,7 @@ def run_ours(args):
                                                 np.array_equal(ge.cpu().numpy(), be4))
         k = min(SAMPLE_ALL, n_mine)
         oc, _ = o.count_sorted(a4_np[lo4:lo4 + k], bs4, be4, threads=cores)
-        parity["headline_counts_1m_sample"] = bool(np.array_equal(c4[:k].cpu().numpy(), oc))
+        parity["headline_counts_4m_sample"] = bool(np.array_equal(c4[:k].cpu().numpy(), oc))
     if dist is not None and lead:
         full = torch.empty(1, dtype=torch.uint64, device=dev)
         db4.count(to_dev(a4_np), counts=False, total=full, method=bits.METHOD_SEARCH)
@@ -469,6 +469,13 @@ def run_ours(args):
         e2e_forms[name] = (ms, l)
     e2e_name = min(e2e_forms, key=lambda k: e2e_forms[k][0])
     e2e_ms, e2e_launches = e2e_forms[e2e_name]
+    # The host link's own rate for the same bytes: a copy-engine transfer of
+    # the page-locked queries into device memory (the bound of the call
+    # above, whose 8-byte query reads dominate its traffic).
+    q_dev = torch.empty_like(a_host, device=dev)
+    link_ms, _, _ = timed(lambda: q_dev.copy_(a_host, non_blocking=True), 3, 2)
+    link_gbs = a_host.numel() * 4 / (link_ms * 1e-3) / 1e9
+    del q_dev
     db4.check()
     parity["headline_host_buffers"] = bool(
         np.array_equal(counts_host.numpy(), c4.cpu().numpy()) and
@@ -582,7 +589,11 @@ def run_ours(args):
                 "ms_per_step": e2e_ms, "gpu_launches": e2e_launches,
                 "call": "bits_count_host on page-locked queries and counts (read and written "
                         "in place by the search kernel over the bus) + the total copied back",
-                "form": e2e_name, "forms_ms": sig({k: v[0] for k, v in e2e_forms.items()})},
+                "form": e2e_name, "forms_ms": sig({k: v[0] for k, v in e2e_forms.items()}),
+                "host_link": sig({"h2d_gbs": link_gbs, "h2d_ms_for_queries": link_ms,
+                                  "frac": link_ms / e2e_ms,
+                                  "what": "copy-engine transfer of the same page-locked "
+                                          "queries to the device, timed alone"})},
         "gpu_launches": launches,
         "clocks": clocks,
         "headline_form": head,

@@ -94,11 +94,8 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
   uint32_t* s_stage = sm;
   uint32_t* s_vstage = sm + kSwTile;  // key/value mode only
   uint32_t* s_wcnt = sm + (KV ? 2 : 1) * kSwTile;  // [warps][kCnt]: per-warp digit counters
-  uint32_t* s_tstart = s_wcnt + kSwWarps * kCnt;
-  uint32_t* s_gbase = s_tstart + kRadix;
-  uint32_t* s_tcount = s_gbase + kRadix;
-  uint32_t* s_dbase = s_tcount + kRadix;
-  uint32_t* s_w = s_dbase + kRadix;
+  uint32_t* s_gbase = s_wcnt + kSwWarps * kCnt;
+  uint32_t* s_w = s_gbase + kRadix;
   uint32_t* s_tile = s_w + kRadix / 32;
 
   const bool y1 = blockIdx.y != 0;
@@ -123,7 +120,6 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
   for (int i = tid; i < kSwWarps * kPeerTableWords; i += kSwBlock) s_stage[i] = 0u;
   const uint32_t hcount = tid < kRadix ? hist[tid] : 0u;
   const uint32_t dbase = scan256_excl(hcount, s_w);  // also publishes *s_tile / s_wcnt
-  if (tid < kRadix) s_dbase[tid] = dbase;
   const uint32_t tile = *s_tile;
   const uint32_t tile_base = tile * (uint32_t)kSwTile;
   const uint32_t warp_base = tile_base + w * 32u * kSwKpt;
@@ -188,14 +184,16 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
       s_wcnt[ww * kCnt + tid] = tcount;
       tcount += c;
     }
-    s_tcount[tid] = tcount;
     // Publish this tile's count as early as possible.
     volatile uint32_t* st = status + (size_t)tile * kRadix + tid;
     *st = (tile == 0 ? kFlagPre : kFlagAgg) | tcount;
   }
   const uint32_t tstart = scan256_excl(tcount, s_w);
   if (tid < kRadix) {
-    s_tstart[tid] = tstart;
+    // Each warp's offset of this digit becomes its position in the tile,
+    // so that staging a key reads one word.
+    #pragma unroll
+    for (int ww = 0; ww < kSwWarps; ++ww) s_wcnt[ww * kCnt + tid] += tstart;
     if (tile == 0) s_gbase[tid] = dbase - tstart;
   }
   __syncthreads();
@@ -207,7 +205,7 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
     if (idx < n) {
       const uint32_t d = (key[k] >> shift) & 255u;
       const uint32_t r = (rank2[k / 2] >> (16 * (k & 1))) & 0xFFFFu;
-      const uint32_t at = s_tstart[d] + s_wcnt[w * kCnt + d] + r;
+      const uint32_t at = s_wcnt[w * kCnt + d] + r;
       if (at < (uint32_t)kSwTile) {
         s_stage[at] = key[k];
         if (KV) {
@@ -253,7 +251,7 @@ k_onesweep(SweepJobs jobs, uint32_t n, uint32_t* __restrict__ err) {
 
 size_t sweep_smem(bool kv) {
   return sizeof(uint32_t) *
-         ((kv ? 2 : 1) * kSwTile + kSwWarps * kCnt + 5 * kRadix + kRadix / 32 + 4);
+         ((kv ? 2 : 1) * kSwTile + kSwWarps * kCnt + kRadix + kRadix / 32 + 4);
 }
 
 // Raises k_onesweep's dynamic shared-memory limit on the current device

@@ -296,6 +296,15 @@ k_sweep_keys(SkJobs J, uint32_t n, uint32_t* __restrict__ err) {
       if (tile == 0) s_gbase[tid] = s_dbase[jb * kRadix + tid] - tstart;
     }
     __syncthreads();
+    // Fold the tile's digit starts into the warps' packed offsets, so that
+    // staging a key reads one word (both halves stay below 2^16: every
+    // position is inside the tile).
+    if (tid < (unsigned)(kRadix / 2)) {
+      const uint32_t add = s_tstart[2 * tid] | (s_tstart[2 * tid + 1] << 16);
+      #pragma unroll
+      for (int ww = 0; ww < kSkWarps; ++ww) s_cnt[ww * kSkCntWords + tid] += add;
+    }
+    __syncthreads();
 
     // Stage the tile in digit order.
     #pragma unroll
@@ -305,8 +314,7 @@ k_sweep_keys(SkJobs J, uint32_t n, uint32_t* __restrict__ err) {
         const uint32_t key = buf_l[pos];
         const uint32_t d = (key >> shift) & 255u;
         const uint32_t r = (rank2[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
-        const uint32_t woff = (wcnt[d >> 1] >> ((d & 1u) << 4)) & 0xFFFFu;
-        const uint32_t at = s_tstart[d] + woff + r;
+        const uint32_t at = ((wcnt[d >> 1] >> ((d & 1u) << 4)) & 0xFFFFu) + r;
         if (at < (uint32_t)kSkTile) buf_s[at] = key;
       }
     }
