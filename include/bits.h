@@ -312,8 +312,8 @@ bits_status bits_project(const uint32_t* d_contig, const uint32_t* d_start, cons
  *   n      0 <= n <= BITS_NOALLOC_MAX_INTERVALS, else BITS_EOVERFLOW.
  *   d_bs   device uint32[n], receives the sorted starts (caller-owned).
  *   d_be   device uint32[n], receives the sorted ends (caller-owned).
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * The first call on a device also looks up the scratch array's device
+ * address (cudaGetSymbolAddress).
  * All calls on a device share the one scratch array: calls that overlap on
  * the GPU (other streams, other host threads) race and must be serialised
  * by the caller.  The call synchronises `stream` (it reads the sort's digit
