@@ -701,6 +701,9 @@ def other_workloads(args, bits, bits_synth, goldens, o, torch, dev, to_dev, time
           "count_qps": n_a / (min(ex_forms.values()) * 1e-3),
           "host_buffers_us": host_ms * 1e3, "build_20m_ms": build_ms,
           "build_keys_per_s": 2 * n_b / (build_ms * 1e-3),
+          # 36 B per key (four 8-bit passes of 8 B plus the split's 4 B) against
+          # the copy bandwidth; the passes are bound by shared memory, not HBM
+          "build_hbm_frac": 36.0 * 2 * n_b / (build_ms * 1e-3) / 1e9 / hbm_peak,
           "one_shot_ms": one_ms}
 
     # projection of 20M chromosome-local closed reads (12 B read + 8 B written each)
