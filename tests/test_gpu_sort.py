@@ -7,7 +7,8 @@ full 32-bit keys (four passes), keys whose top digits are constant (passes
 skipped; an odd number of passes ends with a copy out of the ping-pong
 buffer), starts and ends with different numbers of active passes (one
 array alone in the later passes), all keys equal (no pass at all), heavy
-duplicates from clustered reads, coordinates at 0 and 2^32 - 1, and the
+duplicates from clustered reads, warps whose 32 keys share one digit (the
+peer tables' worst case), coordinates at 0 and 2^32 - 1, and the
 allocation-free entry point writing to outputs that are only 4-byte
 aligned (tiles then come through plain loads instead of bulk copies).
 """
@@ -66,6 +67,24 @@ def test_all_keys_equal_and_extremes():
     check_build(np.tile(np.array([[7, 9]], np.uint32), (20_000, 1)))
     b = np.array([[0, 1], [0, 2**32 - 1], [2**32 - 2, 2**32 - 1], [5, 6]] * 5000, np.uint32)
     check_build(b)
+
+
+def test_warps_sharing_one_digit():
+    # The first pass sees the keys in input order: each run of 32 (one warp's
+    # slot of a tile) has one low digit, every fifth run two digits by lane
+    # parity, so the peer tables see all 32 lanes (or 16) on one word.  The
+    # upper bytes are random, so all four passes run.
+    rng = np.random.default_rng(17)
+    n = 3 * 8192 + 4099
+    i = np.arange(n, dtype=np.int64)
+    low = (i // 32) % 256
+    alt = ((i // 32) % 5 == 0) & (i % 2 == 1)
+    low = np.where(alt, (low + 128) % 256, low)
+    s = (rng.integers(0, 2**23, size=n, dtype=np.int64) << 8) | low
+    e = s + rng.integers(1, 256, size=n, dtype=np.int64)
+    b = np.stack([s, e], axis=1).astype(np.uint32)
+    check_build(b)
+    check_build(b, enumerate=True)   # the key/value sort ranks the same way
 
 
 def test_clustered_duplicates_at_scale():
