@@ -62,7 +62,7 @@ typedef enum bits_status {
 
 typedef enum bits_method {
   BITS_METHOD_AUTO = 0,      /* autotuner picks among the built methods            */
-  BITS_METHOD_SEARCH = 1,    /* shared-memory top tree + per-thread binary search  */
+  BITS_METHOD_SEARCH = 1,    /* shared-memory top + quad-cooperative 16-ary tree   */
   BITS_METHOD_RMI = 2,       /* learned index: predict, bounded search, verify     */
   BITS_METHOD_MERGEPATH = 3  /* sort the queries, co-rank them by merge path       */
 } bits_method;
@@ -184,7 +184,7 @@ bits_status bits_enumerate_pairs(const bits_db* db, const uint32_t* d_a, uint64_
  *   h_observed  host, total of the unshuffled queries (nullable).
  *   h_k_ge      host, #{s : total_s >= observed} (nullable).
  *   h_pvalue    host, (k_ge + 1) / (N + 1) in IEEE double (nullable).
- * method: BITS_METHOD_SEARCH or BITS_METHOD_RMI (AUTO picks).  Synchronises the
+ * method: BITS_METHOD_SEARCH or BITS_METHOD_RMI (AUTO: SEARCH).  Synchronises the
  * stream.  BITS_EINVAL if a query is inverted, lies before the first contig or
  * crosses its contig's end.  Work of one call runs as one persistent launch,
  * replayed from a cached CUDA graph when the same arguments repeat.
@@ -336,8 +336,10 @@ bits_status bits_sort_intervals_noalloc(const uint32_t* d_b, uint64_t n, uint32_
  * method named).  The first bits_count / bits_count_method call of a class
  * that nothing pins times the candidates on the caller's own inputs with
  * CUDA events (batches of back-to-back calls, three alternating rounds) and
- * records the fastest overall (used by BITS_METHOD_AUTO) and the fastest of
- * each method (used by calls that name their method); bits_mc and
+ * records the fastest of each method (used by calls that name their
+ * method) and, for BITS_METHOD_AUTO, the fastest plain search unless another
+ * method is at least 5 % faster (with no record -- parameters pinned, or
+ * under stream capture -- AUTO takes the plain search); bits_mc and
  * bits_count_matrix time their own candidates the same way on their first
  * call of a class.  Nothing is timed under stream capture.  When the
  * environment variable BITS_AUTOTUNE_CACHE names a file, records are read

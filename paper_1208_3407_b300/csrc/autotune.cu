@@ -147,8 +147,9 @@ void tune_store(const char* kind, int la, int lb, int flags, const std::vector<i
 
 TuneCount count_params(const bits_db* db, int method, uint32_t n, bool counts) {
   TuneCount t;
-  t.method = method == BITS_METHOD_AUTO ? (db->has_rmi ? BITS_METHOD_RMI : BITS_METHOD_SEARCH)
-                                        : method;
+  // AUTO without a record (parameters pinned, stream capture) takes the
+  // plain search, the faster form on every shape measured.
+  t.method = method == BITS_METHOD_AUTO ? BITS_METHOD_SEARCH : method;
   std::vector<int> v;
   if (tune_lookup("count", ceil_log2_u64(n), ceil_log2_u64(db->n),
                   count_flags(db, counts, method), &v) &&
@@ -236,14 +237,25 @@ bits_status autotune_count(const bits_db* db, const uint32_t* d_a, uint32_t n,
       if (s != BITS_OK) return finish(s);
       best_ms[c] = std::min(best_ms[c], ms);
     }
-  // Record the fastest overall (AUTO) and the fastest of each method.
+  // Record the fastest of each method, and for AUTO the fastest plain
+  // search unless another method beats it by at least 5 %: on short calls
+  // the batches differ by little more than their timing noise, and a
+  // learned index chosen by noise costs more per query wherever the choice
+  // is reused at larger sizes (the all-pairs kernel applies it to every
+  // query set).
+  int best_of[4] = {-1, -1, -1, -1};
+  for (size_t c = 0; c < cands.size(); ++c) {
+    int& b = best_of[cands[c].method];
+    if (b < 0 || best_ms[c] < best_ms[b]) b = (int)c;
+  }
+  int best_auto = best_of[BITS_METHOD_SEARCH];
+  for (int m : {(int)BITS_METHOD_RMI, (int)BITS_METHOD_MERGEPATH})
+    if (best_of[m] >= 0 && (best_auto < 0 || best_ms[best_of[m]] < 0.95f * best_ms[best_auto]))
+      best_auto = best_of[m];
+  best_of[BITS_METHOD_AUTO] = best_auto;
   for (int m : {(int)BITS_METHOD_AUTO, (int)BITS_METHOD_SEARCH, (int)BITS_METHOD_RMI,
                 (int)BITS_METHOD_MERGEPATH}) {
-    int best = -1;
-    for (size_t c = 0; c < cands.size(); ++c)
-      if ((m == BITS_METHOD_AUTO || cands[c].method == m) &&
-          (best < 0 || best_ms[c] < best_ms[best]))
-        best = (int)c;
+    const int best = best_of[m];
     if (best >= 0)
       tune_store("count", la, lb, count_flags(db, counts, m),
                  {cands[best].method, cands[best].raise, cands[best].block});

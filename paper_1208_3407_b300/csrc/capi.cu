@@ -353,7 +353,9 @@ bits_status bits_mc(const bits_db* db, int32_t method, const uint32_t* d_a, uint
     set_error("bits_mc: at most 2^32 - 1 queries");
     return BITS_EOVERFLOW;
   }
-  if (method == BITS_METHOD_AUTO) method = db->has_rmi ? BITS_METHOD_RMI : BITS_METHOD_SEARCH;
+  // The Monte-Carlo autotuner tunes the work-unit shape, not the method:
+  // AUTO takes the plain search (faster than the learned index here).
+  if (method == BITS_METHOD_AUTO) method = BITS_METHOD_SEARCH;
   if (method == BITS_METHOD_RMI && !db->has_rmi) {
     set_error("bits_mc: database was built without a learned index");
     return BITS_ENOTIMPL;
