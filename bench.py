@@ -756,6 +756,29 @@ def other_workloads(args, bits, bits_synth, goldens, o, torch, dev, to_dev, time
     ap_nodes = sum(x.shape[0] * 2 * tree_levels(y.shape[0]) for x in a5_np for y in b5_np)
     out["allpairs"] = {"ms": ms5, "pair_counts_per_s": n_q5 * len(dbs5) / (ms5 * 1e-3),
                        "roofline_l2_frac": ap_nodes / (ms5 * 1e-3) / l2_peak}
+    # The same matrix with the 64 query sets built as databases too
+    # (bits_count_matrix_db): each pair counted from its smaller side's sorted
+    # keys.  The sets' builds are setup, timed on their own.
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    adbs5 = [bits.Database(x) for x in a5]
+    e1.record(stream)
+    e1.synchronize()
+    build_sets_ms = e0.elapsed_time(e1)
+    m5d = torch.empty_like(m5)
+    bits.count_matrix_db(adbs5, dbs5, out=m5d)   # tunes and captures the graph
+    ms5d, _, _ = timed(lambda: bits.count_matrix_db(adbs5, dbs5, out=m5d),
+                       max(3, min(args.steps, 5)), 3, all_ranks=False)
+    parity["allpairs_db_all_2048_totals"] = bool(np.array_equal(m5d.cpu().numpy(),
+                                                                goldens.read_allpairs_fullsize()))
+    n_keys5 = sum(min(x.shape[0], y.shape[0]) for x in a5_np for y in b5_np)
+    out["allpairs"]["from_databases"] = {
+        "ms": ms5d, "build_query_sets_ms": build_sets_ms,
+        "pair_counts_per_s": n_q5 * len(dbs5) / (ms5d * 1e-3),
+        "searches": n_keys5, "searches_per_s": n_keys5 / (ms5d * 1e-3)}
+    for d in adbs5:
+        d.free()
+    del adbs5, m5d
     # ---- Monte-Carlo screen over the same sets: 4 shuffles per step -------------
     co5, cl5 = bits_synth.mc_contig_table(g5)
     dco5, dcl5 = to_dev(co5), to_dev(cl5)

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (METHOD_AUTO, METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH, BitsError,
                    LIB_PATH)
 
-__all__ = ["Database", "count_matrix", "project", "mc_summary", "mc_matrix", "McStats",
+__all__ = ["Database", "count_matrix", "count_matrix_db", "project", "mc_summary", "mc_matrix", "McStats",
            "set_tuning", "get_tuning", "tuning",
            "kernel_launches", "BitsError", "METHOD_AUTO",
            "METHOD_SEARCH", "METHOD_RMI", "METHOD_MERGEPATH", "LIB_PATH", "device_view"]
@@ -257,6 +257,25 @@ def count_matrix(dbs, a_sets, *, out: torch.Tensor | None = None, stream=None) -
     st = lib.bits_count_matrix(hs, n_db, ps, ns, n_sets, out.data_ptr() if out.numel() else None,
                                _stream_ptr(stream))
     _lib.check(st, "bits_count_matrix")
+    return out
+
+
+def count_matrix_db(a_dbs, b_dbs, *, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """M[i][j] = total(A_i, B_j) with the query sets given as databases too
+    (bits_count_matrix_db): each pair is counted from its smaller side's
+    sorted keys in its larger side's tree."""
+    lib = _lib.load()
+    n_a, n_b = len(a_dbs), len(b_dbs)
+    dev = (a_dbs or b_dbs)[0].device if (a_dbs or b_dbs) else torch.device("cuda")
+    if out is None:
+        out = torch.empty((n_a, n_b), dtype=torch.uint64, device=dev)
+    if out.dtype != torch.uint64 or tuple(out.shape) != (n_a, n_b) or not out.is_contiguous():
+        raise TypeError("out must be a contiguous uint64 tensor of shape (len(a_dbs), len(b_dbs))")
+    ha = (C.c_void_p * max(1, n_a))(*[d._h.value for d in a_dbs])
+    hb = (C.c_void_p * max(1, n_b))(*[d._h.value for d in b_dbs])
+    st = lib.bits_count_matrix_db(ha, n_a, hb, n_b, out.data_ptr() if out.numel() else None,
+                                  _stream_ptr(stream))
+    _lib.check(st, "bits_count_matrix_db")
     return out
 
 

@@ -20,7 +20,7 @@ METHOD_AUTO, METHOD_SEARCH, METHOD_RMI, METHOD_MERGEPATH = range(4)
 
 # Every symbol include/bits.h declares.
 EXPORTS = ["bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc",
-           "bits_count_matrix", "bits_db_info", "bits_check", "bits_free", "bits_last_error", "bits_kernel_launches",
+           "bits_count_matrix", "bits_count_matrix_db", "bits_db_info", "bits_check", "bits_free", "bits_last_error", "bits_kernel_launches",
            "bits_sort_intervals_noalloc", "bits_db_rmi", "bits_selftest_wait", "bits_project",
            "bits_mc_summary", "bits_mc_matrix", "bits_enumerate_offsets", "bits_enumerate_pairs",
            "bits_set_tuning", "bits_get_tuning"]
@@ -67,6 +67,8 @@ def load():
                             C.POINTER(C.c_uint64), C.POINTER(C.c_double), vp]
     lib.bits_count_matrix.argtypes = [C.POINTER(C.c_void_p), C.c_uint32, C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_uint64), C.c_uint32, u64p, vp]
+    lib.bits_count_matrix_db.argtypes = [C.POINTER(C.c_void_p), C.c_uint32,
+                                         C.POINTER(C.c_void_p), C.c_uint32, u64p, vp]
     lib.bits_db_info.argtypes = [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                  C.POINTER(C.c_uint64), C.POINTER(C.c_int32)]
     lib.bits_check.argtypes = [vp, vp]
@@ -85,7 +87,7 @@ def load():
     lib.bits_db_rmi.argtypes = [vp, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32),
                                 C.POINTER(C.c_float), C.POINTER(C.c_float)]
     for f in ("bits_build_db", "bits_count", "bits_count_method", "bits_count_host", "bits_mc",
-              "bits_count_matrix", "bits_db_info", "bits_check", "bits_sort_intervals_noalloc", "bits_db_rmi",
+              "bits_count_matrix", "bits_count_matrix_db", "bits_db_info", "bits_check", "bits_sort_intervals_noalloc", "bits_db_rmi",
               "bits_selftest_wait", "bits_project", "bits_mc_summary", "bits_mc_matrix",
               "bits_enumerate_offsets", "bits_enumerate_pairs", "bits_set_tuning",
               "bits_get_tuning"):

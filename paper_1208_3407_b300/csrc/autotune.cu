@@ -292,14 +292,14 @@ void mc_record(const bits_db* db, int method, uint32_t n, const TuneMc& t) {
 bool mc_pinned() { return g_pin.mc_shuffles > 0 || g_pin.top_raise >= 0; }
 
 int ap_chunk_params(uint64_t total_queries, uint64_t total_db, uint32_t n_db, uint32_t n_sets,
-                    bool* tuned) {
+                    bool* tuned, const char* kind) {
   if (tuned) *tuned = false;
   if (g_pin.ap_chunk > 0) {
     if (tuned) *tuned = true;
     return g_pin.ap_chunk;
   }
   std::vector<int> v;
-  if (tune_lookup("allpairs", ceil_log2_u64(total_queries), ceil_log2_u64(total_db),
+  if (tune_lookup(kind, ceil_log2_u64(total_queries), ceil_log2_u64(total_db),
                   (int)(n_db * 4096u + n_sets), &v) &&
       v.size() == 1) {
     if (tuned) *tuned = true;
@@ -309,8 +309,8 @@ int ap_chunk_params(uint64_t total_queries, uint64_t total_db, uint32_t n_db, ui
 }
 
 void ap_chunk_record(uint64_t total_queries, uint64_t total_db, uint32_t n_db, uint32_t n_sets,
-                     int chunk) {
-  tune_store("allpairs", ceil_log2_u64(total_queries), ceil_log2_u64(total_db),
+                     int chunk, const char* kind) {
+  tune_store(kind, ceil_log2_u64(total_queries), ceil_log2_u64(total_db),
              (int)(n_db * 4096u + n_sets), {chunk});
 }
 

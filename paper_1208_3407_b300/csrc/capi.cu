@@ -395,6 +395,26 @@ bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
                           static_cast<cudaStream_t>(stream));
 }
 
+bits_status bits_count_matrix_db(const bits_db* const* a_dbs, uint32_t n_a,
+                                 const bits_db* const* b_dbs, uint32_t n_b, uint64_t* d_matrix,
+                                 void* stream) {
+  if ((n_a && !a_dbs) || (n_b && !b_dbs) || (n_a && n_b && !d_matrix)) {
+    set_error("bits_count_matrix_db: NULL argument");
+    return BITS_EINVAL;
+  }
+  for (uint32_t i = 0; i < n_a; ++i)
+    if (!a_dbs[i]) {
+      set_error("bits_count_matrix_db: NULL database handle");
+      return BITS_EINVAL;
+    }
+  for (uint32_t j = 0; j < n_b; ++j)
+    if (!b_dbs[j]) {
+      set_error("bits_count_matrix_db: NULL database handle");
+      return BITS_EINVAL;
+    }
+  return run_count_matrix_db(a_dbs, n_a, b_dbs, n_b, d_matrix, static_cast<cudaStream_t>(stream));
+}
+
 bits_status bits_enumerate_offsets(const bits_db* db, const uint32_t* d_a, uint64_t n,
                                    uint64_t* d_offsets, void* stream) {
   if (!db || !d_offsets || (n && !d_a)) {

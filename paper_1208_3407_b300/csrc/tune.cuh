@@ -65,10 +65,12 @@ bool mc_pinned();
 
 // Queries per all-pairs work unit: pinned, else the choice recorded for
 // this argument shape (allpairs.cu times the candidates), else 8192.
+// `kind` separates the record of bits_count_matrix ("allpairs") from that
+// of bits_count_matrix_db ("allpairs_db").
 int ap_chunk_params(uint64_t total_queries, uint64_t total_db, uint32_t n_db, uint32_t n_sets,
-                    bool* tuned);
+                    bool* tuned, const char* kind = "allpairs");
 void ap_chunk_record(uint64_t total_queries, uint64_t total_db, uint32_t n_db, uint32_t n_sets,
-                     int chunk);
+                     int chunk, const char* kind = "allpairs");
 
 // Low-level cache access shared by the tuners.
 bool tune_lookup(const char* kind, int la, int lb, int flags, std::vector<int>* vals);
