@@ -59,6 +59,11 @@ def test_host_side_argument_checks(lib):
     assert lib.bits_mc(None, 0, None, 0, None, None, 0, 0, 0, 0, None, None, None, None,
                        None) == _lib.BITS_EINVAL
     assert lib.bits_count_matrix(None, 1, None, None, 0, None, None) == _lib.BITS_EINVAL
+    assert lib.bits_count_matrix_db(None, 1, None, 0, None, None) == _lib.BITS_EINVAL
+    assert lib.bits_count_matrix_db(None, 0, None, 1, None, None) == _lib.BITS_EINVAL
+    null2 = (C.c_void_p * 2)(None, None)
+    assert lib.bits_count_matrix_db(null2, 2, null2, 2, None, None) == _lib.BITS_EINVAL
+    assert lib.bits_count_matrix_db(None, 0, None, 0, None, None) == _lib.BITS_OK  # empty matrix
     unknown_flag = _lib.Opts(0, 0, 0, 2)
     assert lib.bits_build_db(C.c_void_p(256), 4, C.byref(unknown_flag), None,
                              C.byref(h)) == _lib.BITS_EINVAL
