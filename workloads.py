@@ -13,6 +13,9 @@ Workloads (inputs from the seeded generator ``bits_synth``):
     mc-100k-1m       bits_mc, 100,000 intervals vs 1,000,000, 10,000 shuffles
     allpairs-64x32   bits_count_matrix, 64 query sets x 32 databases
     allpairs-16x8    the same on the first 16 query sets and 8 databases
+    allpairs-db-64x32, allpairs-db-16x8
+                     bits_count_matrix_db on those sets with the query sets
+                     built as databases too
     mc-screen-64x32  bits_mc_matrix over those sets, 4 shuffles, with the summary
     mc-screen-16x8   the same on the first 16 query sets and 8 databases
                      (--shuffles N: shuffles per call, default 4)
@@ -34,7 +37,7 @@ sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 import bits_synth  # noqa: E402
 
 from paper_1208_3407_b300 import (METHOD_MERGEPATH, METHOD_RMI, METHOD_SEARCH,  # noqa: E402
-                                  Database, count_matrix, mc_matrix, set_tuning)
+                                  Database, count_matrix, count_matrix_db, mc_matrix, set_tuning)
 
 METHODS = {"search": METHOD_SEARCH, "rmi": METHOD_RMI, "mergepath": METHOD_MERGEPATH}
 
@@ -115,6 +118,17 @@ def main(argv=None):
         for _ in range(args.reps):
             ms = _timed(lambda: count_matrix(dbs, a, out=out))
         for d in dbs:
+            d.check()
+    elif args.name in ("allpairs-db-64x32", "allpairs-db-16x8"):
+        _, a_sets, b_sets = bits_synth.config5()
+        if args.name == "allpairs-db-16x8":
+            a_sets, b_sets = a_sets[:16], b_sets[:8]
+        a_dbs = [Database(_dev(a)) for a in a_sets]
+        b_dbs = [Database(_dev(b)) for b in b_sets]
+        out = torch.empty((len(a_dbs), len(b_dbs)), dtype=torch.uint64, device="cuda")
+        for _ in range(args.reps):
+            ms = _timed(lambda: count_matrix_db(a_dbs, b_dbs, out=out))
+        for d in a_dbs + b_dbs:
             d.check()
     elif args.name in ("mc-screen-64x32", "mc-screen-16x8"):
         genome, a_sets, b_sets = bits_synth.config5()
