@@ -106,6 +106,27 @@ def test_invariants():
         assert ((c > 0).any()) == (t_ab > 0)                  # decision problem
 
 
+def test_total_from_each_side_sorted_keys():
+    """The rank-sum identity the all-pairs count from databases relies on:
+    summed over A, Algorithm 2's ICount needs each sorted array only on its
+    own, total(A, B) = sum_{x in A_E} #(B_S < x) - sum_{x in A_S} #(B_E <= x),
+    and the same pairs counted from B's side give the mirror image.  Checked
+    against the oracle's brute force (numpy's searchsorted gives the ranks)."""
+    for seed in range(40):
+        a, b = synth.tiny_random(2000 + seed, 37, 23, coord_max=300, max_len=40,
+                                 allow_empty_queries=False)
+        _, brute = O.count_brute(a, b)
+        a_s, a_e = np.sort(a[:, 0]), np.sort(a[:, 1])
+        b_s, b_e = np.sort(b[:, 0]), np.sort(b[:, 1])
+        from_a = int(np.searchsorted(b_s, a_e, side="left").sum()) - \
+            int(np.searchsorted(b_e, a_s, side="right").sum())
+        from_b = int(np.searchsorted(a_s, b_e, side="left").sum()) - \
+            int(np.searchsorted(a_e, b_s, side="right").sum())
+        assert from_a == brute and from_b == brute
+        # the k-th sorted start and end of one side form a valid search pair
+        assert (a_s < a_e).all() and (b_s < b_e).all()
+
+
 def test_config1_full_brute_force():
     a, b = synth.config1()
     c1, t1 = O.count_brute(a, b)
