@@ -248,7 +248,13 @@ bits_status bits_mc_summary(const uint64_t* d_totals, uint32_t n_shuffles, uint3
  * error word of each database they were counted against (bits_check).  The
  * shuffle work of all pairs is one persistent launch, replayed from a cached
  * CUDA graph when the same arguments repeat.  Work units above 2^32 (about
- * 1.1e15 placements) give BITS_EOVERFLOW: split the shuffle range.
+ * 1.1e15 placements) give BITS_EOVERFLOW: split the shuffle range.  When the
+ * sets are large against many databases (searching every placement in every
+ * database would cost at least twice as much) and every query interval is
+ * non-empty and inside its contig, the call instead builds the sets, then
+ * each shuffle's placed sets, as databases of their own and counts every
+ * pair from its smaller side (as bits_count_matrix_db); the same draws give
+ * the same totals, and the call then synchronises the stream.
  */
 bits_status bits_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint32_t* const* d_as,
                            const uint64_t* n_as, uint32_t n_sets, const uint32_t* d_contig_off,

@@ -145,6 +145,70 @@ bits_status read_device_error(const bits_db* db, cudaStream_t st, bool clear) {
   return BITS_OK;
 }
 
+// The sort of bits_build_db: starts into db->bs, ends into db->be (with
+// the enumeration table's index sort when want_enum).
+bits_status sort_database(bits_db* db, const uint32_t* d_b, bool want_enum, cudaStream_t st) {
+  const uint32_t nn = db->n;
+  if (nn) {
+    RadixScratch ws{};
+    const size_t sw = radix_status_words(nn);
+    // With enumeration the sort carries indices: 4 more arrays of n words.
+    const size_t words_n = align_up(sizeof(uint32_t) * nn, 256);
+    const size_t scratch_bytes = (want_enum ? 6 : 2) * words_n +
+                                 align_up(sizeof(uint32_t) * kRadixHistWords, 256) +
+                                 align_up(sizeof(uint32_t) * sw * 8, 256) + 256;
+    void* scratch = nullptr;
+    const bits_status se = pool_alloc(&scratch, scratch_bytes, st);
+    if (se != BITS_OK) return se;
+    char* sb = static_cast<char*>(scratch);
+    ws.tmp_s = reinterpret_cast<uint32_t*>(sb);
+    sb += align_up(sizeof(uint32_t) * nn, 256);
+    ws.tmp_e = reinterpret_cast<uint32_t*>(sb);
+    sb += align_up(sizeof(uint32_t) * nn, 256);
+    ws.hist = reinterpret_cast<uint32_t*>(sb);
+    sb += align_up(sizeof(uint32_t) * kRadixHistWords, 256);
+    ws.status = reinterpret_cast<uint32_t*>(sb);
+    sb += align_up(sizeof(uint32_t) * sw * 8, 256);
+    ws.tickets = reinterpret_cast<uint32_t*>(sb);
+    sb += 256;
+    bits_status s;
+    if (want_enum) {
+      SortSpec spec[2]{};
+      uint32_t* idx_s = reinterpret_cast<uint32_t*>(sb);
+      spec[0].comp = 0;
+      spec[0].out_keys = db->bs;
+      spec[0].tmp_keys = ws.tmp_s;
+      spec[0].out_vals = idx_s;
+      spec[0].tmp_vals = reinterpret_cast<uint32_t*>(sb + words_n);
+      spec[1].comp = 1;
+      spec[1].out_keys = db->be;
+      spec[1].tmp_keys = ws.tmp_e;
+      spec[1].out_vals = reinterpret_cast<uint32_t*>(sb + 2 * words_n);
+      spec[1].tmp_vals = reinterpret_cast<uint32_t*>(sb + 3 * words_n);
+      s = radix_sort_pairs(reinterpret_cast<const uint2*>(d_b), nn, spec, 0, db->err, ws, st,
+                           nullptr);
+      if (s == BITS_OK) s = launch_enum_gather(d_b, idx_s, nn, db->enum_e, st);
+    } else {
+      s = radix_sort_intervals(reinterpret_cast<const uint2*>(d_b), nn, db->bs, db->be, db->err,
+                               ws, st);
+    }
+    pool_free(scratch, st);
+    if (s != BITS_OK) return s;
+  }
+  return BITS_OK;
+}
+
+bits_status db_rebuild(bits_db* db, const uint32_t* d_b, cudaStream_t st) {
+  if (db->has_rmi || db->enum_e) {
+    set_error("db_rebuild: only plain databases are rebuilt in place");
+    return BITS_EINVAL;
+  }
+  BITS_CUDA_TRY(cudaMemsetAsync(db->err, 0, sizeof(uint32_t), st));
+  const bits_status s = sort_database(db, d_b, false, st);
+  if (s != BITS_OK) return s;
+  return build_levels(db, st);
+}
+
 }  // namespace bits
 
 using namespace bits;
@@ -237,50 +301,8 @@ bits_status bits_build_db(const uint32_t* d_b, uint64_t n, const bits_opts* opts
   if (cudaMemsetAsync(db->err, 0, sizeof(uint32_t), st) != cudaSuccess)
     return fail(cuda_status(cudaGetLastError(), "cudaMemsetAsync"));
 
-  if (nn) {
-    RadixScratch ws{};
-    const size_t sw = radix_status_words(nn);
-    // With enumeration the sort carries indices: 4 more arrays of n words.
-    const size_t words_n = align_up(sizeof(uint32_t) * nn, 256);
-    const size_t scratch_bytes = (want_enum ? 6 : 2) * words_n +
-                                 align_up(sizeof(uint32_t) * kRadixHistWords, 256) +
-                                 align_up(sizeof(uint32_t) * sw * 8, 256) + 256;
-    void* scratch = nullptr;
-    const bits_status se = pool_alloc(&scratch, scratch_bytes, st);
-    if (se != BITS_OK) return fail(se);
-    char* sb = static_cast<char*>(scratch);
-    ws.tmp_s = reinterpret_cast<uint32_t*>(sb);
-    sb += align_up(sizeof(uint32_t) * nn, 256);
-    ws.tmp_e = reinterpret_cast<uint32_t*>(sb);
-    sb += align_up(sizeof(uint32_t) * nn, 256);
-    ws.hist = reinterpret_cast<uint32_t*>(sb);
-    sb += align_up(sizeof(uint32_t) * kRadixHistWords, 256);
-    ws.status = reinterpret_cast<uint32_t*>(sb);
-    sb += align_up(sizeof(uint32_t) * sw * 8, 256);
-    ws.tickets = reinterpret_cast<uint32_t*>(sb);
-    sb += 256;
-    bits_status s;
-    if (want_enum) {
-      SortSpec spec[2]{};
-      uint32_t* idx_s = reinterpret_cast<uint32_t*>(sb);
-      spec[0].comp = 0;
-      spec[0].out_keys = db->bs;
-      spec[0].tmp_keys = ws.tmp_s;
-      spec[0].out_vals = idx_s;
-      spec[0].tmp_vals = reinterpret_cast<uint32_t*>(sb + words_n);
-      spec[1].comp = 1;
-      spec[1].out_keys = db->be;
-      spec[1].tmp_keys = ws.tmp_e;
-      spec[1].out_vals = reinterpret_cast<uint32_t*>(sb + 2 * words_n);
-      spec[1].tmp_vals = reinterpret_cast<uint32_t*>(sb + 3 * words_n);
-      s = radix_sort_pairs(reinterpret_cast<const uint2*>(d_b), nn, spec, 0, db->err, ws, st,
-                           nullptr);
-      if (s == BITS_OK) s = launch_enum_gather(d_b, idx_s, nn, db->enum_e, st);
-    } else {
-      s = radix_sort_intervals(reinterpret_cast<const uint2*>(d_b), nn, db->bs, db->be, db->err,
-                               ws, st);
-    }
-    pool_free(scratch, st);
+  {
+    const bits_status s = sort_database(db.get(), d_b, want_enum, st);
     if (s != BITS_OK) return fail(s);
   }
   bits_status s = build_levels(db.get(), st);

@@ -80,4 +80,9 @@ namespace bits {
 // Synchronise `st`, read the database's device error word (and clear it if
 // asked) and turn it into a status.
 bits_status read_device_error(const bits_db* db, cudaStream_t st, bool clear);
+
+// Re-sorts db->n intervals d_b into a plain database (no learned index, no
+// enumeration table) and rebuilds its tree, in its own memory (capi.cu).
+// Synchronises `st` once (the sort reads its histograms back).
+bits_status db_rebuild(bits_db* db, const uint32_t* d_b, cudaStream_t st);
 }  // namespace bits

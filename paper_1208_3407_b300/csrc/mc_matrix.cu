@@ -14,6 +14,18 @@
 // unit prefix sums.  Set i draws Philox at counter (interval, shuffle, i, 0),
 // so its placements are the same against every database and set 0's are
 // the single test's.
+//
+// Because of that, one shuffle's totals for every pair are the all-pairs
+// matrix of the shuffle's placed sets against the databases.  When it pays
+// (the sets' placements searched against every database cost at least
+// twice as much as building the placed sets as databases and counting each
+// pair from its smaller side) and every query interval is non-empty and
+// inside its contig, the screen runs that way instead: per shuffle,
+// k_mc_place writes each set's placed intervals, the placed set is sorted
+// into a database of its own (built on the first shuffle, rebuilt in the
+// same memory afterwards), run_count_matrix_db counts the matrix
+// (allpairs.cu), and k_mc_scatter stores it as that shuffle's totals.  The
+// placements are the same Philox draws, so the totals are the same.
 #include <algorithm>
 #include <map>
 #include <memory>
@@ -21,6 +33,7 @@
 #include <vector>
 
 #include "allpairs.cuh"
+#include "philox.cuh"
 #include "mc_matrix.cuh"
 #include "mc_stats.cuh"
 #include "mc_unit.cuh"
@@ -140,6 +153,146 @@ GraphCache<std::vector<uint64_t>, McMatGraph> g_graphs(16);
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// ---- the screen by databases on both sides --------------------------------
+
+constexpr int kPlaceBlock = 256;
+
+// Sets *flag unless every interval is non-empty and inside its contig.
+__global__ void __launch_bounds__(kPlaceBlock)
+k_mc_screen_check(const uint2* __restrict__ A, uint32_t n, const uint32_t* __restrict__ coff,
+                  const uint32_t* __restrict__ clen, uint32_t nc, uint32_t* __restrict__ flag) {
+  bool bad = false;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint2 q = A[k];
+    const int c = contig_of(coff, nc, q.x);
+    bad |= !(c >= 0 && q.y > q.x &&
+             (unsigned long long)q.y <= (unsigned long long)coff[c] + clen[c]);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+// Interval k of set `set` placed by shuffle s: the draw and the offset of
+// mc_count_chunk (mc_unit.cuh), written out as an interval.
+__global__ void __launch_bounds__(kPlaceBlock)
+k_mc_place(const uint2* __restrict__ A, uint32_t n, uint32_t set, uint32_t s, uint32_t key0,
+           uint32_t key1, const uint32_t* __restrict__ coff, const uint32_t* __restrict__ clen,
+           uint32_t nc, uint2* __restrict__ out) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint2 q = A[k];
+    const int c = contig_of(coff, nc, q.x);  // valid: checked by k_mc_screen_check
+    const uint32_t len = q.y - q.x;
+    const uint32_t rng = clen[c] - len + 1u;
+    const uint4 x = philox4x32_10(make_uint4(k, s, set, 0u), key0, key1);
+    const uint32_t start = coff[c] + philox_offset(x, rng);
+    out[k] = make_uint2(start, start + len);
+  }
+}
+
+// totals[p][s_local] = m[p] for every pair p.
+__global__ void k_mc_scatter(const unsigned long long* __restrict__ m, uint32_t n_pairs,
+                             uint32_t n_shuffles, uint32_t s_local,
+                             unsigned long long* __restrict__ totals) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n_pairs) totals[(size_t)p * n_shuffles + s_local] = m[p];
+}
+
+// Whether the screen by databases pays: the persistent kernel searches every
+// placement in every database; the other way builds each placed set (about
+// four searches' worth of work per interval, measured) and counts each pair
+// from its smaller side.  Small screens stay with the persistent kernel.
+bool screen_by_databases_pays(const bits_db* const* dbs, uint32_t n_db, const uint64_t* n_as,
+                              uint32_t n_sets) {
+  uint64_t sum_a = 0, pairs_min = 0;
+  for (uint32_t i = 0; i < n_sets; ++i) {
+    sum_a += n_as[i];
+    for (uint32_t j = 0; j < n_db; ++j) pairs_min += std::min<uint64_t>(n_as[i], dbs[j]->n);
+  }
+  if (sum_a < (1u << 20)) return false;
+  return 2 * (pairs_min + 4 * sum_a) < sum_a * n_db;
+}
+
+// The observed matrix and every shuffle's totals by databases on both sides,
+// unless an interval is empty or outside its contig (*taken = false: nothing
+// was written).  The sets are built as databases from their own intervals
+// (the observed matrix), then rebuilt in the same memory from each shuffle's
+// placements.
+bits_status run_screen_by_databases(const bits_db* const* dbs, uint32_t n_db,
+                                    const uint32_t* const* d_as, const uint64_t* n_as,
+                                    uint32_t n_sets, const uint32_t* coff, const uint32_t* clen,
+                                    uint32_t nc, uint64_t seed, uint32_t s_begin, uint32_t s_end,
+                                    uint64_t* d_observed, uint64_t* d_totals, cudaStream_t st,
+                                    bool* taken) {
+  *taken = false;
+  uint64_t max_n = 1;
+  for (uint32_t i = 0; i < n_sets; ++i) max_n = std::max<uint64_t>(max_n, n_as[i]);
+  const size_t off_flag = align256(sizeof(uint2) * max_n);
+  const size_t off_m = off_flag + 256;
+  const size_t bytes = off_m + sizeof(uint64_t) * (size_t)n_sets * n_db;
+  void* scratch = nullptr;
+  {
+    const bits_status as = pool_alloc(&scratch, bytes, st);
+    if (as != BITS_OK) return as;
+  }
+  uint2* placed = static_cast<uint2*>(scratch);
+  uint32_t* d_flag = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) + off_flag);
+  uint64_t* d_m = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + off_m);
+  std::vector<bits_db*> sets(n_sets, nullptr);
+  auto finish = [&](bits_status s) {
+    for (bits_db* d : sets) bits_free(d);
+    pool_free(scratch, st);
+    return s;
+  };
+  auto grid_for = [](uint64_t n) {
+    return (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>((n + kPlaceBlock - 1) / kPlaceBlock, (uint64_t)sm_count() * 8));
+  };
+  // Every interval non-empty and inside its contig (one read-back).
+  BITS_CUDA_TRY(cudaMemsetAsync(d_flag, 0, sizeof(uint32_t), st));
+  for (uint32_t i = 0; i < n_sets; ++i)
+    if (n_as[i]) {
+      k_mc_screen_check<<<grid_for(n_as[i]), kPlaceBlock, 0, st>>>(
+          reinterpret_cast<const uint2*>(d_as[i]), (uint32_t)n_as[i], coff, clen, nc, d_flag);
+      count_launch();
+    }
+  uint32_t h_flag = 0;
+  BITS_CUDA_TRY(cudaMemcpyAsync(&h_flag, d_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  BITS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h_flag) return finish(BITS_OK);  // left to the persistent kernel, which flags it
+  *taken = true;
+  const uint32_t n_pairs = n_sets * n_db;
+  for (uint32_t i = 0; i < n_sets; ++i) {
+    const bits_status b = bits_build_db(n_as[i] ? d_as[i] : nullptr, n_as[i], nullptr,
+                                        static_cast<void*>(st), &sets[i]);
+    if (b != BITS_OK) return finish(b);
+  }
+  {
+    const bits_status c = run_count_matrix_db(sets.data(), n_sets, dbs, n_db, d_m, st);
+    if (c != BITS_OK) return finish(c);
+    BITS_CUDA_TRY(cudaMemcpyAsync(d_observed, d_m, sizeof(uint64_t) * n_pairs,
+                                  cudaMemcpyDeviceToDevice, st));
+  }
+  const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+  const uint32_t n_shuffles = s_end - s_begin;
+  for (uint32_t s = s_begin; s < s_end; ++s) {
+    for (uint32_t i = 0; i < n_sets; ++i) {
+      if (!n_as[i]) continue;
+      k_mc_place<<<grid_for(n_as[i]), kPlaceBlock, 0, st>>>(
+          reinterpret_cast<const uint2*>(d_as[i]), (uint32_t)n_as[i], i, s, key0, key1, coff,
+          clen, nc, placed);
+      count_launch();
+      const bits_status b = db_rebuild(sets[i], reinterpret_cast<const uint32_t*>(placed), st);
+      if (b != BITS_OK) return finish(b);
+    }
+    bits_status c = run_count_matrix_db(sets.data(), n_sets, dbs, n_db, d_m, st);
+    if (c != BITS_OK) return finish(c);
+    k_mc_scatter<<<(n_pairs + 255) / 256, 256, 0, st>>>(
+        reinterpret_cast<const unsigned long long*>(d_m), n_pairs, n_shuffles, s - s_begin,
+        reinterpret_cast<unsigned long long*>(d_totals));
+    count_launch();
+  }
+  return finish(BITS_OK);
+}
+
 }  // namespace
 
 bits_status run_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint32_t* const* d_as,
@@ -149,8 +302,21 @@ bits_status run_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint32
                           uint64_t* d_totals, bits_mc_stat* d_stats, cudaStream_t st) {
   const uint32_t n_shuffles = shuffle_end - shuffle_begin;
   if (n_db == 0 || n_sets == 0) return BITS_OK;
+  bits_status s;
+  if (n_shuffles && n_contigs && screen_by_databases_pays(dbs, n_db, n_as, n_sets)) {
+    bool taken = false;
+    s = run_screen_by_databases(dbs, n_db, d_as, n_as, n_sets, d_contig_off, d_contig_len,
+                                n_contigs, seed, shuffle_begin, shuffle_end, d_observed, d_totals,
+                                st, &taken);
+    if (s != BITS_OK) return s;
+    if (taken) {
+      if (d_stats)
+        return launch_mc_summary(d_totals, n_shuffles, n_sets * n_db, d_observed, d_stats, st);
+      return BITS_OK;
+    }
+  }
   // Observed matrix: Algorithm 2 for every pair (the all-pairs kernel).
-  bits_status s = run_count_matrix(dbs, n_db, d_as, n_as, n_sets, d_observed, st);
+  s = run_count_matrix(dbs, n_db, d_as, n_as, n_sets, d_observed, st);
   if (s != BITS_OK) return s;
   std::vector<uint64_t> key = {reinterpret_cast<uintptr_t>(d_totals), seed, shuffle_begin,
                                shuffle_end, reinterpret_cast<uintptr_t>(d_contig_off),

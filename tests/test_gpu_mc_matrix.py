@@ -219,3 +219,32 @@ def test_screen_larger_sampled(bits):
         np.testing.assert_array_equal(tot[i, j], t)
         assert obs[i, j] == o
         assert_stat(st[i * 4 + j], O.mc_summary(t, o), where=(i, j))
+
+
+def test_screen_by_databases(bits):
+    """Sets far larger than many small databases: the screen builds each
+    shuffle's placed sets as databases and counts every pair from its
+    smaller side.  Every total, observed count and summary equals the
+    oracle's; shuffle ranges split and rejoin; with one empty query interval
+    (which no database may hold) the same screen runs in the persistent
+    kernel and gives the same totals."""
+    sizes_a = [400_000, 350_000, 300_000]
+    sizes_b = [2_000, 1_500, 2_500, 1_000, 3_000, 2_200, 900, 1_800, 2_600, 1_200, 2_000, 1_700]
+    genome, a_sets, b_sets = _screen_inputs(sizes_a, sizes_b, seed=31)
+    obs, tot, st = _gpu_screen(bits, genome, a_sets, b_sets, 4242, 0, 6)
+    oobs, otot = _oracle_screen(genome, a_sets, b_sets, 4242, 0, 6)
+    np.testing.assert_array_equal(obs, oobs)
+    np.testing.assert_array_equal(tot, otot)
+    for i in range(len(a_sets)):
+        for j in range(len(b_sets)):
+            assert_stat(st[i * len(b_sets) + j], O.mc_summary(otot[i, j], int(oobs[i, j])),
+                        where=(i, j))
+    _, t_lo, _ = _gpu_screen(bits, genome, a_sets, b_sets, 4242, 0, 2, stats=False)
+    _, t_hi, _ = _gpu_screen(bits, genome, a_sets, b_sets, 4242, 2, 6, stats=False)
+    np.testing.assert_array_equal(np.concatenate([t_lo, t_hi], axis=2), tot)
+    empty = [a.copy() for a in a_sets]
+    empty[1][7, 1] = empty[1][7, 0]
+    obs_e, tot_e, _ = _gpu_screen(bits, genome, empty, b_sets, 4242, 0, 6, stats=False)
+    oobs_e, otot_e = _oracle_screen(genome, empty, b_sets, 4242, 0, 6)
+    np.testing.assert_array_equal(tot_e, otot_e)
+    np.testing.assert_array_equal(obs_e, oobs_e)
