@@ -146,8 +146,10 @@ bits_status read_device_error(const bits_db* db, cudaStream_t st, bool clear) {
 }
 
 // The sort of bits_build_db: starts into db->bs, ends into db->be (with
-// the enumeration table's index sort when want_enum).
-bits_status sort_database(bits_db* db, const uint32_t* d_b, bool want_enum, cudaStream_t st) {
+// the enumeration table's index sort when want_enum).  read_back = false:
+// the keys-only sort runs without reading anything back (inputs checked).
+bits_status sort_database(bits_db* db, const uint32_t* d_b, bool want_enum, cudaStream_t st,
+                          bool read_back = true) {
   const uint32_t nn = db->n;
   if (nn) {
     RadixScratch ws{};
@@ -190,7 +192,7 @@ bits_status sort_database(bits_db* db, const uint32_t* d_b, bool want_enum, cuda
       if (s == BITS_OK) s = launch_enum_gather(d_b, idx_s, nn, db->enum_e, st);
     } else {
       s = radix_sort_intervals(reinterpret_cast<const uint2*>(d_b), nn, db->bs, db->be, db->err,
-                               ws, st);
+                               ws, st, read_back);
     }
     pool_free(scratch, st);
     if (s != BITS_OK) return s;
@@ -204,7 +206,7 @@ bits_status db_rebuild(bits_db* db, const uint32_t* d_b, cudaStream_t st) {
     return BITS_EINVAL;
   }
   BITS_CUDA_TRY(cudaMemsetAsync(db->err, 0, sizeof(uint32_t), st));
-  const bits_status s = sort_database(db, d_b, false, st);
+  const bits_status s = sort_database(db, d_b, false, st, false);
   if (s != BITS_OK) return s;
   return build_levels(db, st);
 }

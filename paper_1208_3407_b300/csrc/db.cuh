@@ -83,6 +83,7 @@ bits_status read_device_error(const bits_db* db, cudaStream_t st, bool clear);
 
 // Re-sorts db->n intervals d_b into a plain database (no learned index, no
 // enumeration table) and rebuilds its tree, in its own memory (capi.cu).
-// Synchronises `st` once (the sort reads its histograms back).
+// Nothing is read back (every sort pass runs): the caller has checked that
+// every interval has start < end.
 bits_status db_rebuild(bits_db* db, const uint32_t* d_b, cudaStream_t st);
 }  // namespace bits

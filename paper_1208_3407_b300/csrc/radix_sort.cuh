@@ -48,8 +48,14 @@ bits_status radix_sort_pairs(const uint2* d_src, uint32_t n, const SortSpec spec
                              uint32_t* d_err, RadixScratch& ws, cudaStream_t st,
                              bool* any_inverted);
 
-// The database sort: starts into out_s, ends into out_e (keys only).
+// The database sort: starts into out_s, ends into out_e (keys only).  With
+// read_back (the default) it reads the digit histograms on the host
+// (synchronising `st` once), skips passes whose digit is the same for every
+// key and returns BITS_EINVAL for an interval with end <= start; without it
+// nothing is read back, every pass runs and such an interval only sets
+// d_err (for inputs already checked).
 bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, uint32_t* out_e,
-                                 uint32_t* d_err, RadixScratch& ws, cudaStream_t st);
+                                 uint32_t* d_err, RadixScratch& ws, cudaStream_t st,
+                                 bool read_back = true);
 
 }  // namespace bits

@@ -342,7 +342,8 @@ k_sweep_keys(SkJobs J, uint32_t n, uint32_t* __restrict__ err) {
 }  // namespace
 
 bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, uint32_t* out_e,
-                                 uint32_t* d_err, RadixScratch& ws, cudaStream_t st) {
+                                 uint32_t* d_err, RadixScratch& ws, cudaStream_t st,
+                                 bool read_back) {
   if (n == 0) return BITS_OK;
   const uint32_t tiles = (n + kSkTile - 1) / kSkTile;
   const size_t status_words = (size_t)tiles * kRadix;
@@ -352,26 +353,32 @@ bits_status radix_sort_intervals(const uint2* d_b, uint32_t n, uint32_t* out_s, 
   k_split_hist<<<split_grid, kSplitBlock, 0, st>>>(d_b, n, out_s, out_e, ws.hist, d_err);
   BITS_LAUNCH_CHECK("k_split_hist");
 
-  uint32_t h_hist[2 * kPasses * kRadix];
-  uint32_t h_err = 0;
-  BITS_CUDA_TRY(cudaMemcpyAsync(h_hist, ws.hist, sizeof(h_hist), cudaMemcpyDeviceToHost, st));
-  BITS_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  BITS_CUDA_TRY(cudaStreamSynchronize(st));
-  if (h_err & DEV_ERR_INVALID) {
-    set_error("a database interval has end <= start");
-    return BITS_EINVAL;
-  }
-
   // Active passes per array: a pass whose digit is the same for every key
-  // keeps the order and is skipped (keys all equal: no pass at all).
+  // keeps the order and is skipped (keys all equal: no pass at all).  That
+  // takes the histograms on the host; without the read-back every pass runs
+  // (the result is the same) and an invalid interval only sets d_err.
   int passes[2][kPasses], np[2] = {0, 0};
-  for (int a = 0; a < 2; ++a)
-    for (int p = 0; p < kPasses; ++p) {
-      bool constant = false;
-      for (int d = 0; d < kRadix; ++d)
-        if (h_hist[(a * kPasses + p) * kRadix + d] == n) constant = true;
-      if (!constant) passes[a][np[a]++] = p;
+  if (read_back) {
+    uint32_t h_hist[2 * kPasses * kRadix];
+    uint32_t h_err = 0;
+    BITS_CUDA_TRY(cudaMemcpyAsync(h_hist, ws.hist, sizeof(h_hist), cudaMemcpyDeviceToHost, st));
+    BITS_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    BITS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_err & DEV_ERR_INVALID) {
+      set_error("a database interval has end <= start");
+      return BITS_EINVAL;
     }
+    for (int a = 0; a < 2; ++a)
+      for (int p = 0; p < kPasses; ++p) {
+        bool constant = false;
+        for (int d = 0; d < kRadix; ++d)
+          if (h_hist[(a * kPasses + p) * kRadix + d] == n) constant = true;
+        if (!constant) passes[a][np[a]++] = p;
+      }
+  } else {
+    for (int a = 0; a < 2; ++a)
+      for (int p = 0; p < kPasses; ++p) passes[a][np[a]++] = p;
+  }
   const int steps = std::max(np[0], np[1]);
   if (steps == 0) return BITS_OK;
   BITS_CUDA_TRY(cudaMemsetAsync(ws.status, 0, sizeof(uint32_t) * status_words * 2 * steps, st));
