@@ -254,7 +254,8 @@ bits_status bits_mc_summary(const uint64_t* d_totals, uint32_t n_shuffles, uint3
  * non-empty and inside its contig, the call instead builds the sets, then
  * each shuffle's placed sets, as databases of their own and counts every
  * pair from its smaller side (as bits_count_matrix_db); the same draws give
- * the same totals, and the call then synchronises the stream.
+ * the same totals, and the call then returns only after the device has
+ * finished its work (it frees the sets' databases, as bits_free does).
  */
 bits_status bits_mc_matrix(const bits_db* const* dbs, uint32_t n_db, const uint32_t* const* d_as,
                            const uint64_t* n_as, uint32_t n_sets, const uint32_t* d_contig_off,
