@@ -130,6 +130,125 @@ k_allpairs(MatArgs P) {
   }
 }
 
+// ---- rank sums by merge path (bits_count_matrix_db, pairs of similar size) --
+//
+// For sorted X and Y, sum_{x in X} #(Y < x) (strict) or #(Y <= x) is read off
+// the merge of the two arrays in which an element of Y goes before x exactly
+// when it is counted: each x adds the number of Y elements merged before it.
+// The merge is cut into tiles of kMgTile merged positions; a tile boundary at
+// diagonal d splits it into the first i elements of X and d - i of Y (merge
+// path: the binary search of merge_split).  A CTA stages one tile's X and Y
+// elements in shared memory, each thread finds its own diagonal in the tile
+// and merges kMgPer positions sequentially.  Both arrays are read once.
+constexpr int kMgBlock = 256;
+constexpr uint32_t kMgTile = 4096;                 // merged positions per tile
+constexpr uint32_t kMgPer = kMgTile / kMgBlock;   // per thread
+
+struct MergeJob {
+  const uint32_t* x;
+  const uint32_t* y;
+  uint32_t nx, ny;
+  uint32_t strict;       // 1: counts #(Y < x); 0: #(Y <= x)
+  uint32_t negate;       // the sum is subtracted from the entry
+  uint32_t out;          // matrix entry
+  uint32_t first_tile;   // its first tile among all jobs' tiles
+  uint32_t first_split;  // its first tile boundary (tiles + 1 per job)
+};
+
+struct MergeArgs {
+  const MergeJob* jobs;
+  uint32_t n_jobs, n_tiles, n_splits;
+  uint32_t* splits;
+  unsigned long long* matrix;
+};
+
+// x goes before y in the merge: y is not counted for x.
+__device__ __forceinline__ bool x_first(uint32_t x, uint32_t y, bool strict) {
+  return strict ? x <= y : x < y;
+}
+
+// Elements of X among the first d merged positions.
+template <typename P>
+__device__ __forceinline__ uint32_t merge_split(P X, uint32_t nx, P Y, uint32_t ny, uint64_t d,
+                                                bool strict) {
+  uint32_t lo = d > ny ? (uint32_t)(d - ny) : 0u;
+  uint32_t hi = (uint32_t)(d < nx ? d : nx);
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (x_first(X[mid], Y[d - mid - 1], strict)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Last job whose field `first` is <= v (jobs ordered by it).
+__device__ __forceinline__ uint32_t find_job(const MergeJob* jobs, uint32_t n, uint32_t v,
+                                             bool by_tile) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    const uint32_t f = by_tile ? jobs[mid].first_tile : jobs[mid].first_split;
+    if (f <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_merge_splits(MergeArgs P) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < P.n_splits;
+       b += gridDim.x * blockDim.x) {
+    const MergeJob J = P.jobs[find_job(P.jobs, P.n_jobs, b, false)];
+    const uint64_t total = (uint64_t)J.nx + J.ny;
+    const uint64_t d = min((uint64_t)(b - J.first_split) * kMgTile, total);
+    P.splits[b] = merge_split(J.x, J.nx, J.y, J.ny, d, J.strict != 0);
+  }
+}
+
+__global__ void __launch_bounds__(kMgBlock)
+k_merge_sums(MergeArgs P) {
+  __shared__ uint32_t s_buf[kMgTile];
+  __shared__ unsigned long long s_red[32];
+  // Each CTA takes a contiguous run of tiles, so it finds a job once and
+  // then walks its tiles in order.
+  const uint32_t per = (P.n_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t t_begin = min(P.n_tiles, blockIdx.x * per);
+  const uint32_t t_end = min(P.n_tiles, t_begin + per);
+  uint32_t jb = t_begin < t_end ? find_job(P.jobs, P.n_jobs, t_begin, true) : 0u;
+  for (uint32_t t = t_begin; t < t_end; ++t) {
+    while (jb + 1 < P.n_jobs && P.jobs[jb + 1].first_tile <= t) ++jb;
+    const MergeJob J = P.jobs[jb];
+    const bool strict = J.strict != 0;
+    const uint32_t k = t - J.first_tile;
+    const uint64_t total = (uint64_t)J.nx + J.ny;
+    const uint64_t d0 = (uint64_t)k * kMgTile;
+    const uint64_t d1 = min(d0 + kMgTile, total);
+    const uint32_t i0 = P.splits[J.first_split + k], i1 = P.splits[J.first_split + k + 1];
+    const uint32_t j0 = (uint32_t)(d0 - i0), j1 = (uint32_t)(d1 - i1);
+    const uint32_t lx = i1 - i0, ly = j1 - j0;
+    __syncthreads();  // the previous tile is done with s_buf
+    for (uint32_t e = threadIdx.x; e < lx; e += kMgBlock) s_buf[e] = J.x[i0 + e];
+    for (uint32_t e = threadIdx.x; e < ly; e += kMgBlock) s_buf[lx + e] = J.y[j0 + e];
+    __syncthreads();
+    const uint32_t* sx = s_buf;
+    const uint32_t* sy = s_buf + lx;
+    const uint32_t len = lx + ly;
+    const uint32_t e0 = min(threadIdx.x * kMgPer, len), e1 = min(e0 + kMgPer, len);
+    uint32_t a = merge_split(sx, lx, sy, ly, e0, strict), b = e0 - a;
+    unsigned long long sum = 0ull;
+    for (uint32_t e = e0; e < e1; ++e) {
+      const bool take_x = a < lx && (b >= ly || x_first(sx[a], sy[b], strict));
+      if (take_x) {
+        sum += j0 + b;  // the Y elements merged before this x
+        ++a;
+      } else {
+        ++b;
+      }
+    }
+    const unsigned long long s = block_sum_u64(sum, s_red);
+    if (threadIdx.x == 0 && s) atomicAdd(P.matrix + J.out, J.negate ? 0ull - s : s);
+  }
+}
+
 template <bool kSorted>
 int ap_blocks_per_sm(size_t smem) {
   return kernel_blocks_per_sm(reinterpret_cast<const void*>(k_allpairs<kSorted>), kApBlock, smem);
@@ -138,12 +257,14 @@ int ap_blocks_per_sm(size_t smem) {
 struct MatGraph {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
-  void* dev = nullptr;  // descriptors | units | source pointers | ticket
+  void* dev = nullptr;    // descriptors | units | source pointers | ticket
+  void* merge = nullptr;  // merge jobs | tile boundaries (bits_count_matrix_db)
   uint64_t kernels = 0;
   ~MatGraph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (dev) cudaFree(dev);
+    if (merge) cudaFree(merge);
   }
 };
 
@@ -162,7 +283,9 @@ bits_status build_matrix_graph(MatGraph& g, const std::vector<MatDb>& hd,
                                const std::function<std::vector<MatUnit>(uint32_t)>& make_units,
                                const char* tune_kind, uint64_t total_q, uint64_t total_db,
                                uint32_t n_sets, uint64_t* d_matrix, size_t n_out,
-                               cudaStream_t st) {
+                               cudaStream_t st,
+                               const std::function<void(cudaStream_t)>& extra = {},
+                               uint32_t extra_kernels = 0) {
   const uint32_t n_db = (uint32_t)hd.size();
   bool tuned = false;
   uint32_t chunk =
@@ -246,13 +369,14 @@ bits_status build_matrix_graph(MatGraph& g, const std::vector<MatDb>& hd,
   cudaMemsetAsync(d_matrix, 0, sizeof(uint64_t) * n_out, cap);
   cudaMemsetAsync(P.ticket, 0, sizeof(uint32_t), cap);
   k_allpairs<kSorted><<<grid, kApBlock, smem, cap>>>(P);
+  if (extra) extra(cap);
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(cap, &graph);
   cudaStreamDestroy(cap);
   if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture(count_matrix)");
   g.graph = graph;
   BITS_CUDA_TRY(cudaGraphInstantiate(&g.exec, graph, 0));
-  g.kernels = 1;
+  g.kernels = 1 + extra_kernels;
   return BITS_OK;
 }
 
@@ -380,15 +504,36 @@ bits_status run_count_matrix_db(const bits_db* const* a_dbs, uint32_t n_a,
     struct Pair {
       uint32_t tree, src, n, out;
     };
+    // Pairs of similar size (the larger side at most kMergeRatio times the
+    // smaller) are counted by merging the sorted arrays (k_merge_sums):
+    // streaming both costs less than searching every key; the others by
+    // searches (k_allpairs<true>).
+    constexpr uint64_t kMergeRatio = 8;
     std::vector<Pair> pairs;
+    std::vector<MergeJob> jobs;
+    uint32_t n_tiles = 0, n_splits = 0;
     uint64_t total_keys = 0;
     for (uint32_t i = 0; i < n_a; ++i)
       for (uint32_t j = 0; j < n_b; ++j) {
         const bool a_keys = a_dbs[i]->n <= b_dbs[j]->n;
         const Pair p{a_keys ? n_a + j : i, a_keys ? i : n_a + j,
                      a_keys ? a_dbs[i]->n : b_dbs[j]->n, i * n_b + j};
-        total_keys += p.n;
-        if (p.n) pairs.push_back(p);
+        if (!p.n) continue;
+        const bits_db* K = all[p.src];
+        const bits_db* T = all[p.tree];
+        if ((uint64_t)T->n <= kMergeRatio * p.n) {
+          // total = sum_{x in K_E} #(T_S < x) - sum_{x in K_S} #(T_E <= x)
+          const uint32_t tiles = (uint32_t)(((uint64_t)K->n + T->n + kMgTile - 1) / kMgTile);
+          jobs.push_back(MergeJob{K->be, T->bs, K->n, T->n, 1u, 0u, p.out, n_tiles, n_splits});
+          n_tiles += tiles;
+          n_splits += tiles + 1;
+          jobs.push_back(MergeJob{K->bs, T->be, K->n, T->n, 0u, 1u, p.out, n_tiles, n_splits});
+          n_tiles += tiles;
+          n_splits += tiles + 1;
+        } else {
+          total_keys += p.n;
+          pairs.push_back(p);
+        }
       }
     // Units: largest tree first (deepest searches start early), `chunk` keys each.
     std::stable_sort(pairs.begin(), pairs.end(), [&](const Pair& x, const Pair& y) {
@@ -405,9 +550,34 @@ bits_status run_count_matrix_db(const bits_db* const* a_dbs, uint32_t n_a,
     uint64_t total_db = 0;
     for (uint32_t k = 0; k < n_all; ++k) total_db += all[k]->n;
     g = std::make_shared<MatGraph>();
+    MergeArgs M{};
+    std::function<void(cudaStream_t)> merges;
+    if (!jobs.empty()) {
+      const size_t off_splits = align256(sizeof(MergeJob) * jobs.size());
+      BITS_CUDA_TRY(cudaMalloc(&g->merge, off_splits + sizeof(uint32_t) * (size_t)n_splits));
+      BITS_CUDA_TRY(cudaMemcpy(g->merge, jobs.data(), sizeof(MergeJob) * jobs.size(),
+                               cudaMemcpyHostToDevice));
+      M.jobs = static_cast<const MergeJob*>(g->merge);
+      M.n_jobs = (uint32_t)jobs.size();
+      M.n_tiles = n_tiles;
+      M.n_splits = n_splits;
+      M.splits = reinterpret_cast<uint32_t*>(static_cast<char*>(g->merge) + off_splits);
+      M.matrix = reinterpret_cast<unsigned long long*>(d_matrix);
+      const uint32_t grid_s = std::max<uint32_t>(
+          1, std::min<uint32_t>((n_splits + 255) / 256, (uint32_t)sm_count() * 8));
+      const int per_sm =
+          kernel_blocks_per_sm(reinterpret_cast<const void*>(k_merge_sums), kMgBlock, 0);
+      const uint32_t grid_m =
+          std::max<uint32_t>(1, std::min<uint32_t>(n_tiles, (uint32_t)(per_sm * sm_count())));
+      merges = [M, grid_s, grid_m](cudaStream_t cs) {
+        k_merge_splits<<<grid_s, 256, 0, cs>>>(M);
+        k_merge_sums<<<grid_m, kMgBlock, 0, cs>>>(M);
+      };
+    }
     const bits_status s = build_matrix_graph<true>(*g, hd, keys, max_top, make_units,
                                                    "allpairs_db", total_keys, total_db, n_a, d_matrix,
-                                                   (size_t)n_a * n_b, st);
+                                                   (size_t)n_a * n_b, st, merges,
+                                                   jobs.empty() ? 0u : 2u);
     if (s != BITS_OK) return s;
     g_graphs.put(key, g);
   }
