@@ -284,15 +284,18 @@ bits_status bits_count_matrix(const bits_db* const* dbs, uint32_t n_db,
  * 2's sum of ICount over A splits into one rank sum per array,
  *     total(A, B) = sum_{x in A_E} #(B_S < x) - sum_{x in A_S} #(B_E <= x),
  * and counting the same pairs from B's side gives the mirror image, so each
- * pair is counted from its smaller side's keys searched in its larger side's
- * tree: min(|A_i|, |B_j|) searches instead of |A_i|, with the keys in order.
+ * pair is counted from its smaller side's keys: searched in its larger
+ * side's tree (min(|A_i|, |B_j|) searches instead of |A_i|, keys in order),
+ * or, when the two sides are within a factor 8 in size, read off a merge of
+ * the sorted arrays.
  *   a_dbs, n_a  host array of the query sets' database handles.
  *   b_dbs, n_b  host array of the databases' handles (all on this device).
  *   d_matrix    device uint64[n_a][n_b], row-major.
  * Gives the same matrix as bits_count_matrix on the sets' intervals (database
  * intervals are never empty or inverted, so no query is left out).  One
  * persistent launch over (key chunk, tree) work units, largest tree first,
- * replayed from a cached CUDA graph; asynchronous.
+ * and two over the merge tiles, replayed from a cached CUDA graph;
+ * asynchronous.
  */
 bits_status bits_count_matrix_db(const bits_db* const* a_dbs, uint32_t n_a,
                                  const bits_db* const* b_dbs, uint32_t n_b, uint64_t* d_matrix,

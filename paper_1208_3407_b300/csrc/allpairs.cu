@@ -27,7 +27,10 @@
 // against the larger side is #(T_S < x_E) - #(T_E < x_S + 1), exactly a
 // query's.  A pair then costs min(|A|, |B|) searches instead of |A|, and the
 // keys arrive sorted, so neighbouring searches share tree nodes in L1 and
-// L2.  Units are as above with the larger side as the database.
+// L2.  Units are as above with the larger side as the database.  Pairs whose
+// sides are within a factor kMergeRatio in size skip the searches: both rank
+// sums are read off merges of the sorted arrays (k_merge_splits,
+// k_merge_sums below), which read each array once.
 //
 // Each call (zero M, reset the ticket, the persistent launch) is captured
 // once per argument set into a CUDA graph and replayed.
