@@ -207,33 +207,68 @@ __global__ void k_merge_splits(MergeArgs P) {
   }
 }
 
+// One tile's place in its merge.
+struct MgTile {
+  uint32_t job, i0, j0, lx, ly;
+};
+
+__device__ __forceinline__ MgTile tile_of(const MergeArgs& P, uint32_t& jb, uint32_t t) {
+  while (jb + 1 < P.n_jobs && P.jobs[jb + 1].first_tile <= t) ++jb;
+  const MergeJob& J = P.jobs[jb];
+  const uint32_t k = t - J.first_tile;
+  const uint64_t total = (uint64_t)J.nx + J.ny;
+  const uint64_t d0 = (uint64_t)k * kMgTile;
+  const uint64_t d1 = min(d0 + kMgTile, total);
+  const uint32_t i0 = P.splits[J.first_split + k], i1 = P.splits[J.first_split + k + 1];
+  const uint32_t j0 = (uint32_t)(d0 - i0), j1 = (uint32_t)(d1 - i1);
+  return MgTile{jb, i0, j0, i1 - i0, j1 - j0};
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+
+// Starts the copy of a tile's X then Y elements into buf (asynchronous).
+__device__ __forceinline__ void stage_tile(const MergeArgs& P, const MgTile& T, uint32_t* buf) {
+  const MergeJob& J = P.jobs[T.job];
+  for (uint32_t e = threadIdx.x; e < T.lx; e += kMgBlock) cp_async4(buf + e, J.x + T.i0 + e);
+  for (uint32_t e = threadIdx.x; e < T.ly; e += kMgBlock)
+    cp_async4(buf + T.lx + e, J.y + T.j0 + e);
+}
+
 __global__ void __launch_bounds__(kMgBlock)
 k_merge_sums(MergeArgs P) {
-  __shared__ uint32_t s_buf[kMgTile];
+  __shared__ uint32_t s_buf[2][kMgTile];
   __shared__ unsigned long long s_red[32];
   // Each CTA takes a contiguous run of tiles, so it finds a job once and
-  // then walks its tiles in order.
+  // then walks its tiles in order; the next tile streams into the other
+  // buffer (cp.async) while this one is merged.
   const uint32_t per = (P.n_tiles + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = min(P.n_tiles, blockIdx.x * per);
   const uint32_t t_end = min(P.n_tiles, t_begin + per);
-  uint32_t jb = t_begin < t_end ? find_job(P.jobs, P.n_jobs, t_begin, true) : 0u;
+  if (t_begin >= t_end) return;
+  uint32_t jb = find_job(P.jobs, P.n_jobs, t_begin, true);
+  MgTile cur = tile_of(P, jb, t_begin);
+  stage_tile(P, cur, s_buf[0]);
+  asm volatile("cp.async.commit_group;" ::: "memory");
   for (uint32_t t = t_begin; t < t_end; ++t) {
-    while (jb + 1 < P.n_jobs && P.jobs[jb + 1].first_tile <= t) ++jb;
-    const MergeJob J = P.jobs[jb];
-    const bool strict = J.strict != 0;
-    const uint32_t k = t - J.first_tile;
-    const uint64_t total = (uint64_t)J.nx + J.ny;
-    const uint64_t d0 = (uint64_t)k * kMgTile;
-    const uint64_t d1 = min(d0 + kMgTile, total);
-    const uint32_t i0 = P.splits[J.first_split + k], i1 = P.splits[J.first_split + k + 1];
-    const uint32_t j0 = (uint32_t)(d0 - i0), j1 = (uint32_t)(d1 - i1);
-    const uint32_t lx = i1 - i0, ly = j1 - j0;
-    __syncthreads();  // the previous tile is done with s_buf
-    for (uint32_t e = threadIdx.x; e < lx; e += kMgBlock) s_buf[e] = J.x[i0 + e];
-    for (uint32_t e = threadIdx.x; e < ly; e += kMgBlock) s_buf[lx + e] = J.y[j0 + e];
+    const uint32_t slot = (t - t_begin) & 1u;
+    MgTile next{};
+    if (t + 1 < t_end) {
+      next = tile_of(P, jb, t + 1);
+      stage_tile(P, next, s_buf[slot ^ 1u]);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's copies are done
     __syncthreads();
-    const uint32_t* sx = s_buf;
-    const uint32_t* sy = s_buf + lx;
+    const MergeJob& J = P.jobs[cur.job];
+    const bool strict = J.strict != 0;
+    const uint32_t lx = cur.lx, ly = cur.ly, j0 = cur.j0;
+    const uint32_t* sx = s_buf[slot];
+    const uint32_t* sy = sx + lx;
     const uint32_t len = lx + ly;
     const uint32_t e0 = min(threadIdx.x * kMgPer, len), e1 = min(e0 + kMgPer, len);
     uint32_t a = merge_split(sx, lx, sy, ly, e0, strict), b = e0 - a;
@@ -249,7 +284,10 @@ k_merge_sums(MergeArgs P) {
     }
     const unsigned long long s = block_sum_u64(sum, s_red);
     if (threadIdx.x == 0 && s) atomicAdd(P.matrix + J.out, J.negate ? 0ull - s : s);
+    __syncthreads();  // every thread is done with s_buf[slot] before it is refilled
+    cur = next;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 template <bool kSorted>
