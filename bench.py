@@ -15,13 +15,14 @@ Also reported on the same line (most important last, so that a reader of
 the line's tail sees them): the random-read rates the search kernels are
 set against, the exome-vs-reads workload (200,000 queries vs 20,000,000
 reads: count forms, host-buffer count, build, one-shot build+count,
-projection, enumeration), the 64 x 32 all-pairs count and Monte-Carlo
-screen, the 100M database build, the headline's forms, and the Monte-Carlo
+projection, enumeration), the 64 x 32 all-pairs count (from the query sets'
+intervals, and from databases on both sides) and Monte-Carlo screen, the
+100M database build, the headline's forms, and the Monte-Carlo
 significance test (100,000 intervals vs 1,000,000, 10,000 shuffles per
 launch: shuffles/s, placements/s, its L2 and issue rooflines).  Parity is
 checked in the run: every headline count of a 4M-query sample and the
 sorted arrays against the CPU oracle, all 10,000 Monte-Carlo totals and all
-2,048 all-pairs totals against the oracle's stored values.
+2,048 all-pairs totals (both forms) against the oracle's stored values.
 
 The CPU oracle is timed on this host (rank 0) by the protocol both arms
 share: count of a 4,000,000-query sample of the headline against the
