@@ -29,15 +29,19 @@ extern "C" {
  *   bytes             a multiple of the access size, at most 2^32 - 1 accesses.
  *   n_reads           accesses to make, 1 .. 2^34 (rounded up to whole rounds
  *                     of the grid).
- *   nodes_per_access  1: one 64-byte node per access; 2: both 64-byte halves
- *                     of one random 128-byte line, read as two node loads (a
- *                     query whose start and end searches meet in one
- *                     interleaved node pair).
+ *   access_kind       1: one 64-byte node per access (a quad's load);
+ *                     2: both 64-byte halves of one random 128-byte line,
+ *                     read as two quad loads (a query of the quad descent
+ *                     whose start and end searches meet in one interleaved
+ *                     node pair); 3: the same line read by one load
+ *                     instruction of eight lanes (the octet descent).
  *   h_accesses_per_s  host double receiving the accesses per second.
- * Synchronises `stream`.
+ * Returns BITS_EINVAL (nothing launched) for a NULL pointer, an access_kind
+ * outside 1..3, a misaligned or wrongly sized buffer, or n_reads out of
+ * range.  Synchronises `stream`.
  */
 bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes, uint64_t n_reads,
-                                    int32_t nodes_per_access, double* h_accesses_per_s,
+                                    int32_t access_kind, double* h_accesses_per_s,
                                     void* stream);
 
 #ifdef __cplusplus

@@ -2,9 +2,10 @@
 //
 // One thread per query (Sec. "Parallel BITS" assigns one ICount per thread): a coalesced
 // 8-byte load of (start, end), the two top-level searches in shared memory,
-// the quad-cooperative descent through the 16-ary levels (search.cuh), a
-// coalesced 4-byte store of the count, and a block reduction of the 64-bit
-// total with one atomic per CTA.
+// the octet descent through the 16-ary levels (below: one load instruction
+// reads both of a query's nodes), a coalesced 4-byte store of
+// the count, and a block reduction of the 64-bit total with one atomic per
+// CTA.
 //
 // The tree the searches descend is written by levels.cu.
 #include "count.cuh"
@@ -12,6 +13,81 @@
 
 namespace bits {
 namespace {
+
+// x[i] for a lane-dependent i < 8 (a select chain: registers cannot be
+// indexed at run time).
+__device__ __forceinline__ uint32_t select8(const uint32_t (&x)[8], uint32_t i) {
+  uint32_t r = x[0];
+  #pragma unroll
+  for (int o = 1; o < 8; ++o) r = i == (uint32_t)o ? x[o] : r;
+  return r;
+}
+
+// Octet descent: the same searches as quad_descend (both enter at the top
+// level J), with the two nodes of one query read by ONE load instruction.
+// Eight lanes own eight queries; lanes 0-3 of the octet walk the starts'
+// node of query o and lanes 4-7 the ends' node of the same query, so the
+// instruction covers line is and line ie of the interleaved copy, which are
+// one 128-byte line when the two searches share their node index (nearly
+// always on the upper levels; at level 0 when the query's count is small).
+// This part serves a random line read by one instruction at the rate of a
+// single 64-byte node, and the same line read by two loads at half of it
+// (the random-read probe, access kinds 2 and 3), so each shared index saves
+// one memory request.  Used where the searches are bound by memory requests
+// (databases far larger than L2); the quad descent stays where instruction
+// issue binds.
+__device__ __forceinline__ void octet_descend(const LevelIndex& L, uint32_t& is_out,
+                                              uint32_t key_s, uint32_t& ie_out, uint32_t key_e,
+                                              bool stream_level0 = true) {
+  const unsigned lane = lane_id(), sub = lane & 3u, half = (lane >> 2) & 1u;
+  const unsigned obase = lane & ~7u;
+  const uint64_t pol_last = policy_evict_last();
+  const uint64_t pol_first = stream_level0 ? policy_evict_first() : pol_last;
+  // Gather: a starts lane needs (is, key_s) of each query of its octet, an
+  // ends lane (ie, key_e).  After swapping the ends' pair with lane ^ 4, one
+  // shuffle per query and value serves both halves: for queries 0-3 the
+  // starts lanes read lane o and the ends lanes lane o + 4 (which then holds
+  // query o's ends pair); for queries 4-7 the other way round.
+  const uint32_t x_ie = __shfl_xor_sync(0xFFFFFFFFu, ie_out, 4);
+  const uint32_t x_ke = __shfl_xor_sync(0xFFFFFFFFu, key_e, 4);
+  const uint32_t lo_r = half ? x_ie : is_out, lo_k = half ? x_ke : key_s;
+  const uint32_t hi_r = half ? is_out : x_ie, hi_k = half ? key_s : x_ke;
+  uint32_t ix[8], kx[8];
+  #pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const unsigned src = obase | (unsigned)(half ? (o ^ 4) : o);
+    ix[o] = __shfl_sync(0xFFFFFFFFu, o < 4 ? lo_r : hi_r, src);
+    kx[o] = __shfl_sync(0xFFFFFFFFu, o < 4 ? lo_k : hi_k, src);
+  }
+  #pragma unroll
+  for (int j = kMaxLevels - 1; j >= 1; --j) {
+    if (j > L.J) continue;
+    const uint32_t lenj = L.len[j], lenm = L.len[j - 1];
+    // Node i of level j - 1: starts at il + 32 i, ends at il + 32 i + 16.
+    const uint32_t* LX = L.il[j - 1] + 16u * half + 4u * sub;
+    const uint64_t pol = j == 1 ? pol_first : pol_last;
+    uint4 v[8];
+    #pragma unroll
+    for (int o = 0; o < 8; ++o)
+      v[o] = ix[o] < lenj ? ldg4_hint(LX + 32u * ix[o], pol)
+                          : make_uint4(kU32Max, kU32Max, kU32Max, kU32Max);
+    #pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      uint32_t c = cnt4(v[o], kx[o]);
+      c += __shfl_xor_sync(0xFFFFFFFFu, c, 1);
+      c += __shfl_xor_sync(0xFFFFFFFFu, c, 2);
+      ix[o] = ix[o] < lenj ? 16u * ix[o] + c : lenm;
+    }
+  }
+  // Scatter back: lane o of the octet takes its starts rank from a starts
+  // lane and its ends rank from an ends lane, mirroring the gather.
+  const uint32_t o = lane & 7u;
+  const uint32_t a = __shfl_sync(0xFFFFFFFFu, select8(ix, o), obase | o);
+  const uint32_t b = __shfl_sync(0xFFFFFFFFu, select8(ix, o ^ 4u), obase | (o ^ 4u));
+  is_out = o < 4u ? a : b;
+  ie_out = o < 4u ? b : a;
+}
+
 
 // Zeroes the total that k_count_search accumulates into, then lets the
 // count kernel, launched right behind it as a programmatic dependent, start
@@ -46,7 +122,7 @@ k_count_search(const uint2* __restrict__ a, uint32_t n, LevelIndex L, uint32_t n
     const uint32_t key_s = q.y, key_e = q.x + 1u;
     uint32_t rs, re;
     top_rank2(s_top, L.top_size, key_s, key_e, rs, re);
-    quad_descend(L, rs, key_s, re, key_e);
+    octet_descend(L, rs, key_s, re, key_e);
     uint32_t c = icount_from_ranks(rs, re, q.x, nb);
     if (q.y < q.x) {
       c = 0u;

@@ -12,9 +12,11 @@
 // This probe issues exactly that access -- quads reading uniformly random
 // nodes of a buffer, four independent accesses in flight per quad -- and
 // times it with CUDA events, so the search kernels can be set against the
-// same hardware limit.  In pair mode every access reads both 64-byte halves
-// of one random 128-byte line, as a query does whose two searches (starts
-// and ends) meet in one interleaved node pair.
+// same hardware limit.  Access kinds 2 and 3 read both 64-byte halves of one
+// random 128-byte line, as a query does whose two searches (starts and ends)
+// meet in one interleaved node pair: kind 2 with two loads, kind 3 with one
+// load instruction of eight lanes.  The rate follows the number of load
+// requests, not the bytes: kind 3 runs at the kind-1 rate, kind 2 at half.
 #include "common.cuh"
 #include "../../include/bits_probe.h"
 
@@ -34,27 +36,34 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   return x;
 }
 
-// kPair = false: one 64-byte node per random access.  kPair = true: both
-// 64-byte halves of one random 128-byte line, read as two node loads -- the
-// access of a query whose two searches meet in one interleaved node pair.
-template <bool kPair>
+// One random access per (group, k): kind 1, a 64-byte node loaded by a quad
+// (16 bytes a lane); kind 2, both 64-byte halves of one random 128-byte
+// line loaded by a quad as two node loads (the access of the quad descent
+// when a query's two searches meet in one interleaved node pair); kind 3,
+// the same line loaded by an octet with ONE instruction (the octet descent).
+// An octet is two quads, so it makes twice a quad's accesses per round and
+// every kind makes the same number of accesses per round of the grid.
+template <int kKind>
 __global__ void __launch_bounds__(kProbeBlock)
 k_probe_random(const uint4* __restrict__ buf, uint64_t n_units, uint32_t iters,
                unsigned long long* __restrict__ sink) {
+  constexpr uint32_t kLanes = kKind == 3 ? 8u : 4u;          // lanes per access
+  constexpr uint32_t kUnit = kKind == 1 ? 4u : 8u;           // 16-byte words per access
+  constexpr int kFlight = kKind == 3 ? 2 * kProbeInFlight : kProbeInFlight;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t quad = tid >> 2, sub = tid & 3u;
+  const uint32_t grp = tid / kLanes, sub = tid % kLanes;
   uint32_t acc = 0;
   for (uint32_t it = 0; it < iters; ++it) {
-    uint4 v[kProbeInFlight], w[kProbeInFlight];
+    uint4 v[kFlight], w[kFlight];
 #pragma unroll
-    for (int k = 0; k < kProbeInFlight; ++k) {
-      const uint32_t h = mix32(quad * 0x9E3779B9u + (it * kProbeInFlight + k) * 0x632BE5ABu);
+    for (int k = 0; k < kFlight; ++k) {
+      const uint32_t h = mix32(grp * 0x9E3779B9u + (it * kFlight + k) * 0x632BE5ABu);
       const uint64_t unit = ((uint64_t)h * n_units) >> 32;  // < n_units
-      const uint4* p = buf + unit * (kPair ? 8u : 4u) + sub;
+      const uint4* p = buf + unit * kUnit + sub;
       asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
                    : "=r"(v[k].x), "=r"(v[k].y), "=r"(v[k].z), "=r"(v[k].w)
                    : "l"(p));
-      if (kPair) {
+      if (kKind == 2) {
         asm volatile("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
                      : "=r"(w[k].x), "=r"(w[k].y), "=r"(w[k].z), "=r"(w[k].w)
                      : "l"(p + 4));
@@ -63,7 +72,7 @@ k_probe_random(const uint4* __restrict__ buf, uint64_t n_units, uint32_t iters,
       }
     }
 #pragma unroll
-    for (int k = 0; k < kProbeInFlight; ++k) acc += v[k].x ^ v[k].w ^ w[k].y;
+    for (int k = 0; k < kFlight; ++k) acc += v[k].x ^ v[k].w ^ w[k].y;
   }
   // Keeps the loads alive: the result depends on the data read, so the
   // compiler cannot drop them (taken with probability 2^-32 per thread).
@@ -76,21 +85,21 @@ k_probe_random(const uint4* __restrict__ buf, uint64_t n_units, uint32_t iters,
 using namespace bits;
 
 extern "C" bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes,
-                                               uint64_t n_reads, int32_t nodes_per_access,
+                                               uint64_t n_reads, int32_t access_kind,
                                                double* h_accesses_per_s, void* stream) {
   if (!d_buf || !h_accesses_per_s) {
     set_error("bits_probe_random_reads: NULL argument");
     return BITS_EINVAL;
   }
-  if (nodes_per_access != 1 && nodes_per_access != 2) {
-    set_error("bits_probe_random_reads: nodes_per_access must be 1 or 2");
+  if (access_kind < 1 || access_kind > 3) {
+    set_error("bits_probe_random_reads: access_kind must be 1, 2 or 3");
     return BITS_EINVAL;
   }
-  const uint64_t unit = 64ull * (uint64_t)nodes_per_access;
+  const uint64_t unit = access_kind == 1 ? 64ull : 128ull;
   if (bytes < unit || bytes % unit || bytes / unit >= (1ull << 32) ||
       reinterpret_cast<uintptr_t>(d_buf) % unit) {
     set_error("bits_probe_random_reads: the buffer must be aligned to and hold 1 .. 2^32 - 1 "
-              "whole accesses (64 bytes, or 128 with two nodes per access)");
+              "whole accesses (64 bytes for access kind 1, else 128)");
     return BITS_EINVAL;
   }
   if (n_reads == 0 || n_reads > (1ull << 34)) {
@@ -113,10 +122,12 @@ extern "C" bits_status bits_probe_random_reads(const void* d_buf, uint64_t bytes
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
   if (e == cudaSuccess) {
     const uint4* b = static_cast<const uint4*>(d_buf);
-    if (nodes_per_access == 2)
-      k_probe_random<true><<<blocks, kProbeBlock, 0, st>>>(b, bytes / unit, iters, sink);
+    if (access_kind == 3)
+      k_probe_random<3><<<blocks, kProbeBlock, 0, st>>>(b, bytes / unit, iters, sink);
+    else if (access_kind == 2)
+      k_probe_random<2><<<blocks, kProbeBlock, 0, st>>>(b, bytes / unit, iters, sink);
     else
-      k_probe_random<false><<<blocks, kProbeBlock, 0, st>>>(b, bytes / unit, iters, sink);
+      k_probe_random<1><<<blocks, kProbeBlock, 0, st>>>(b, bytes / unit, iters, sink);
     count_launch();
     e = cudaGetLastError();
   }

@@ -19,8 +19,10 @@
 // counted with two shuffles.  Levels 0 .. J-1 are stored interleaved: node
 // i of the starts' level j and node i of the ends' level j share one
 // 128-byte line.  The two ranks of a query differ by its count, so for
-// queries that meet few database intervals both searches read the same
-// node index, and the pair costs one random DRAM line instead of two.
+// queries that meet few database intervals (and on the upper levels for
+// nearly all) both searches read the same node index: one line, which the
+// count kernel's octet descent (count.cu) reads with one load instruction,
+// one memory request instead of the quad descent's two.
 // Only the level-0 nodes normally come from DRAM; the levels above them
 // are 1/16, 1/256, ... of the array and stay in L2.
 #pragma once

@@ -37,17 +37,20 @@ def load():
 
 
 def probe_random_reads(nbytes: int = 4 << 30, n_reads: int = 1 << 24, *, pairs: bool = False,
-                       device=None, stream=None) -> float:
+                       one_load: bool = False, device=None, stream=None) -> float:
     """bits_probe_random_reads on a fresh ``nbytes`` device buffer: random
-    accesses per second, each one 64-byte node (or, with ``pairs``, both
-    halves of one 128-byte line)."""
+    accesses per second, each one 64-byte node (access kind 1), or, with
+    ``pairs``, both halves of one 128-byte line read by two loads (kind 2) or,
+    with ``one_load`` as well, by one load instruction (kind 3)."""
+    if one_load and not pairs:
+        raise ValueError("one_load reads a whole 128-byte line: it needs pairs=True")
+    kind = (3 if one_load else 2) if pairs else 1
     buf = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
     rate = C.c_double()
     s = stream if stream is not None else torch.cuda.current_stream(buf.device)
     with torch.cuda.device(buf.device):
-        _lib.check(load().bits_probe_random_reads(buf.data_ptr(), nbytes, n_reads,
-                                                  2 if pairs else 1, C.byref(rate),
-                                                  int(s.cuda_stream)),
+        _lib.check(load().bits_probe_random_reads(buf.data_ptr(), nbytes, n_reads, kind,
+                                                  C.byref(rate), int(s.cuda_stream)),
                    "bits_probe_random_reads")
     del buf
     return rate.value

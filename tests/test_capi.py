@@ -126,8 +126,10 @@ def test_probe_library_exports_and_checks(lib):
     assert f(None, 1 << 20, 1, 1, C.byref(rate), None) == _lib.BITS_EINVAL
     assert f(C.c_void_p(256), 100, 1, 1, C.byref(rate), None) == _lib.BITS_EINVAL
     assert f(C.c_void_p(256), 1 << 20, 0, 1, C.byref(rate), None) == _lib.BITS_EINVAL
-    assert f(C.c_void_p(256), 1 << 20, 1, 3, C.byref(rate), None) == _lib.BITS_EINVAL
+    assert f(C.c_void_p(256), 1 << 20, 1, 0, C.byref(rate), None) == _lib.BITS_EINVAL
+    assert f(C.c_void_p(256), 1 << 20, 1, 4, C.byref(rate), None) == _lib.BITS_EINVAL
     assert f(C.c_void_p(64), 1 << 20, 1, 2, C.byref(rate), None) == _lib.BITS_EINVAL
+    assert f(C.c_void_p(64), 1 << 20, 1, 3, C.byref(rate), None) == _lib.BITS_EINVAL
     assert b"bits_probe_random_reads" in lib.bits_last_error()
 
 

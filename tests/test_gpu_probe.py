@@ -28,6 +28,11 @@ def test_dram_rate_is_plausible_and_below_l2_rate(bits):
     pairs = max(bits.probe_random_reads(4 << 30, 1 << 24, pairs=True) for _ in range(2))
     assert 1e9 < pairs < 6.4e12 / 128
     assert pairs < 1.1 * dram
+    # The same lines read by one load instruction each: never slower than
+    # two loads, and within the byte rate.
+    line = max(bits.probe_random_reads(4 << 30, 1 << 24, pairs=True, one_load=True)
+               for _ in range(2))
+    assert 0.9 * pairs < line < 6.4e12 / 128
 
 
 def test_argument_errors(bits):
@@ -44,4 +49,8 @@ def test_argument_errors(bits):
                                        None) == 0
     assert lib.bits_probe_random_reads(buf.data_ptr(), 1 << 20, 1 << 16, 2, C.byref(rate),
                                        None) == 0
+    assert lib.bits_probe_random_reads(buf.data_ptr(), 1 << 20, 1 << 16, 3, C.byref(rate),
+                                       None) == 0
+    assert lib.bits_probe_random_reads(buf.data_ptr() + 64, 1 << 16, 16, 3, C.byref(rate),
+                                       None) == 1
     assert rate.value > 0
