@@ -100,6 +100,25 @@ def test_config2_full(bits):
     assert_parity(bits, a, b)
 
 
+@pytest.mark.parametrize("top", [2, 12])
+def test_long_and_short_queries_share_octets(bits, top):
+    # The count kernel reads a query's starts node and ends node of a level
+    # with one load by eight lanes.  Point-like queries keep the two ranks in
+    # one node; queries spanning a quarter of the line separate them on every
+    # level.  Mixed lane by lane, with a ragged last octet and warp.
+    rng = np.random.default_rng(91)
+    nb = 200_000
+    bs = rng.integers(0, 1 << 31, nb, dtype=np.uint64)
+    b = np.stack([bs, bs + 1 + rng.integers(0, 100_000, nb, dtype=np.uint64)], 1)
+    na = 8 * 1237 + 5
+    s = rng.integers(0, 1 << 31, na, dtype=np.uint64)
+    lens = np.where(np.arange(na) % 3 == 0, rng.integers(1 << 24, 1 << 30, na, dtype=np.uint64),
+                    rng.integers(1, 10, na, dtype=np.uint64))
+    a = np.stack([s, s + lens], 1)
+    assert_parity(bits, a.astype(np.uint32), b.astype(np.uint32), check_sort=False,
+                  top_tree_log2=top)
+
+
 def test_constant_digits_are_skipped_correctly(bits):
     # Keys < 2^24 (top digit constant), and a database of identical intervals
     # (every digit constant).
